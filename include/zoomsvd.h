@@ -1,0 +1,210 @@
+/*
+ * zoomsvd.h - C ABI of the GB300 range-SVD library (Zoom-SVD, arXiv 1805.00754).
+ *
+ * The library keeps a compressed store of a growing T x n multi-series matrix
+ * A (rows = time, columns = series; the paper's c is n here) and answers
+ * "SVD of rows [t_s, t_e]" from it without the raw rows.
+ *
+ *   storage phase  (Section 3.2, Algorithm 1, Def. 1-2): A is cut into blocks
+ *                  of b rows; block i is kept as its rank-k truncated SVD
+ *                  U_i (rows_i x k), sigma_i (k), V_i (n x k).
+ *   query phase    (Section 3.3, Algorithm 2-3, Def. 3-4, Eq. 5-9):
+ *                  Partial-SVD of the two boundary blocks, SVD of the stacked
+ *                  Sigma_i V_i^T slabs (Stitched-SVD), then the lift
+ *                  U = diag(S:E) U_r.
+ *
+ * Conventions for every call:
+ *   - Rows are 0-based; a range [t_s, t_e] is inclusive and holds
+ *     t_e - t_s + 1 rows (Problem 1, Section 2.3).
+ *   - Matrices are row-major.  "device" pointers are CUDA global-memory
+ *     addresses on the store's device; "host" pointers are ordinary memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without waiting unless
+ *     stated otherwise; results are ready when the stream reaches that point.
+ *   - Every call returns a zs_status; nothing throws across the ABI.  On an
+ *     error the store is unchanged unless stated otherwise, and
+ *     zs_last_error() gives a one-line message for the calling thread.
+ *   - Results are written in the store's factor type: double for a ZS_F64
+ *     store, float for ZS_F32 and ZS_BF16 stores.
+ */
+#ifndef ZOOMSVD_H
+#define ZOOMSVD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ZS_OK = 0,
+    ZS_EINVAL = 1,      /* bad argument (null pointer, size, config)        */
+    ZS_ERANGE = 2,      /* t_s < 0, t_s > t_e, or t_e >= rows appended      */
+    ZS_ENOMEM = 3,      /* device or host allocation failed / capacity full */
+    ZS_EBUSY = 4,       /* serving queue full; try again                    */
+    ZS_ETIMEDOUT = 5,   /* a bounded wait ran out                           */
+    ZS_EDTYPE = 6,      /* unsupported dtype combination                    */
+    ZS_ECUDA = 7,       /* a CUDA runtime call failed                       */
+    ZS_EINTERNAL = 8,   /* invariant violated inside the library            */
+    ZS_ENOTFOUND = 9    /* unknown ticket / block index                     */
+} zs_status;
+
+typedef enum { ZS_F64 = 0, ZS_F32 = 1, ZS_BF16 = 2 } zs_dtype;
+
+/* Store flags. */
+enum {
+    /* Re-solve each small eigen core (k x k, Rayleigh-Ritz m x m) in FP64
+     * after the FP32 Jacobi sweeps: FP64-accumulated Rayleigh quotient and one
+     * FP64 Jacobi refinement sweep.  No effect on ZS_F64 stores (all FP64).  */
+    ZS_FLAG_FP64_REFINE = 1
+};
+
+typedef struct zs_store zs_store;
+typedef struct zs_server zs_server;
+
+typedef struct {
+    int64_t n;              /* series (columns), 1..1024                     */
+    int64_t b;              /* block rows (Def. 1), >= 1                     */
+    int32_t k;              /* stored rank per block, 1..64, <= n            */
+    int32_t in_dtype;       /* zs_dtype of the rows given to zs_store_append */
+    int64_t capacity_rows;  /* most rows the store will ever hold; the store
+                               preallocates its factor arrays for this many */
+    int32_t device;         /* CUDA device ordinal                           */
+    int32_t flags;          /* ZS_FLAG_*                                     */
+} zs_store_config;
+
+/* Caller-owned device buffers for one query result (factor type). */
+typedef struct {
+    void* U;          /* (t_e - t_s + 1) x k_out, row stride ldu (elements) */
+    int64_t ldu;      /* >= k_out                                            */
+    void* S;          /* k_out singular values, descending                   */
+    void* V;          /* n x k_out, row stride ldv (elements)               */
+    int64_t ldv;      /* >= k_out                                            */
+    int32_t* rank;    /* device int32: number of nonzero singular values;
+                         may be NULL                                          */
+} zs_result;
+
+/* ------------------------------------------------------------------------
+ * Store (Def. 2: the sets U, S, V).
+ * ------------------------------------------------------------------------ */
+
+/* Create an empty store on cfg->device.  Allocates the factor arrays for
+ * cfg->capacity_rows rows (ceil(capacity_rows / b) blocks of
+ * b*k + k + k*n factor elements each) plus the open-block staging buffer.
+ * *out receives the handle (owned by the caller; free with
+ * zs_store_destroy).  ZS_EINVAL on a bad config, ZS_EDTYPE on an unknown
+ * dtype, ZS_ENOMEM if the device allocation fails.                         */
+zs_status zs_store_create(const zs_store_config* cfg, zs_store** out);
+
+/* Destroy a store and free its device memory.  Waits for work the library
+ * enqueued on its own streams; the caller must not use the handle after.   */
+void zs_store_destroy(zs_store* st);
+
+/* Storage phase (Algorithm 1, Def. 1; Theorem 1 cost model).
+ * Append nrows rows (row stride ld >= n elements of cfg.in_dtype; bf16 as
+ * raw 16-bit patterns) to the matrix.  rows_on_device selects whether `rows`
+ * is a device pointer (1) or a host pointer (0; copied before the call
+ * returns, so the caller may reuse it).  Every block completed by these
+ * rows is compressed to its rank-k truncated SVD; the rows of the still-open
+ * last block are kept on the device and that block is (re)compressed as it
+ * stands, so a query may touch every appended row (reading: a short block is
+ * the paper's "current block" of Def. 1).  Work is enqueued on `stream`;
+ * other streams must order after it before querying the new rows.
+ * ZS_ENOMEM if capacity_rows would be exceeded (nothing appended).          */
+zs_status zs_store_append(zs_store* st, const void* rows, int64_t nrows, int64_t ld,
+                          int32_t rows_on_device, void* stream);
+
+/* Host-side counters: rows appended, blocks (closed + open), and device
+ * bytes held by the compressed factors (Theorem 3).  Any pointer may be
+ * NULL.                                                                     */
+zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
+                        int64_t* factor_bytes);
+
+/* Copy block i's stored factors into caller device buffers: U (rows_i x k,
+ * ld k), sigma (k), Vt (k x n, ld n), on `stream`.  *rows_i and *k_i (host)
+ * receive the block's row count and kept rank min(k, rows_i, n); columns
+ * past k_i are zero.  ZS_ENOTFOUND for i outside [0, nblocks).            */
+zs_status zs_store_export_block(const zs_store* st, int64_t i, void* U, void* sigma, void* Vt,
+                                int32_t* rows_i, int32_t* k_i, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Query phase (Algorithm 2 with Partial-SVD Algorithm 3; Eq. 5-9).
+ * ------------------------------------------------------------------------ */
+
+/* SVD of rows [t_s, t_e] of the stored (rank-k per block) matrix, truncated
+ * to k_out = 1..64 columns: U ((t_e-t_s+1) x k_out), S (k_out), V (n x
+ * k_out) into *res.  Columns past the range's rank are zero.  Each pair
+ * (u_j, v_j) is signed so that the largest-|.| entry of v_j is positive
+ * (lowest index on ties).  ZS_ERANGE for a bad range.  Enqueued on stream;
+ * the library's scratch is reused by the next call on the same store, so
+ * calls on one store are serialised by the library.                        */
+zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out,
+                   const zs_result* res, void* stream);
+
+/* nq queries in one batch (host arrays ts[nq], te[nq], results[nq]), all
+ * with width k_out.  Planning is done on the host; the device work is a
+ * fixed set of persistent work-list kernels (replayed as one CUDA graph
+ * when the batch shape fits the captured capacity).  Each result equals
+ * the one zs_query gives for the same range.  ZS_ERANGE if any range is
+ * bad (nothing enqueued).                                                  */
+zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
+                         int32_t k_out, const zs_result* results, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of range queries (no counterpart in the
+ * paper; it serves the paper's query phase to concurrent callers).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t max_batch;        /* most queries launched in one batch          */
+    int32_t max_inflight;     /* batches on the device at once (streams)     */
+    int32_t queue_capacity;   /* pending requests before submit says EBUSY   */
+    int64_t memory_budget;    /* device scratch bytes all in-flight batches
+                                 may hold; requests wait until it frees up   */
+} zs_serve_config;
+
+typedef struct {
+    int64_t completed;
+    int64_t rejected;         /* submits refused with ZS_EBUSY              */
+    int64_t batches;
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* submit -> result ready     */
+    double wall_s;            /* start -> stop                               */
+    double queries_per_s;     /* completed / wall_s                          */
+    double mean_batch;
+} zs_serve_stats;
+
+/* Start a serving thread on the store's device.  The store must outlive the
+ * server.  Appends may continue on other streams; a request sees the rows
+ * whose append call returned before the request was submitted.            */
+zs_status zs_serve_start(zs_store* st, const zs_serve_config* cfg, zs_server** out);
+
+/* Queue one range query; dst holds caller device buffers that must stay
+ * valid until the request is done.  Non-blocking.  *ticket identifies it.
+ * ZS_EBUSY when the queue is full, ZS_ERANGE for a bad range.             */
+zs_status zs_serve_submit(zs_server* sv, int64_t t_s, int64_t t_e, int32_t k_out,
+                          const zs_result* dst, uint64_t* ticket);
+
+/* *done = 1 once the request's results are on the device (and *req_status
+ * holds its status), else 0.  ZS_ENOTFOUND for an unknown ticket.          */
+zs_status zs_serve_poll(zs_server* sv, uint64_t ticket, int32_t* done, int32_t* req_status);
+
+/* Block until the request is done or timeout_ms passes (ZS_ETIMEDOUT).     */
+zs_status zs_serve_wait(zs_server* sv, uint64_t ticket, int64_t timeout_ms, int32_t* req_status);
+
+/* Drain queued requests, stop the thread, fill *stats (may be NULL) and
+ * free the server.                                                        */
+zs_status zs_serve_stop(zs_server* sv, zs_serve_stats* stats);
+
+/* ------------------------------------------------------------------------
+ * Misc.
+ * ------------------------------------------------------------------------ */
+const char* zs_status_str(zs_status s);
+const char* zs_last_error(void);
+
+/* Number of kernel launches the library has issued in this process (all
+ * stores), for launch accounting.                                          */
+int64_t zs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZOOMSVD_H */

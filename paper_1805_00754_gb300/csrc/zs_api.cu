@@ -1,0 +1,538 @@
+// zs_api.cu - host runtime behind the C ABI in include/zoomsvd.h: the device
+// store (Def. 2), the storage-phase driver (Algorithm 1 block by block, with
+// double-buffered host->device staging), query planning (Algorithm 3's index
+// arithmetic) and the batch executor that runs the query kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "zoomsvd.h"
+#include "zs_api_internal.h"
+#include "zs_internal.h"
+
+namespace zs {
+int64_t launch_count_total();
+
+thread_local std::string g_last_error;
+
+zs_status fail(zs_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+zs_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(ZS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ZS_CU(call, what)                                     \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
+    } while (0)
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != prev_) cudaSetDevice(prev_);
+    }
+
+   private:
+    int prev_ = 0;
+};
+
+static size_t in_size(int dt) { return dt == ZS_F64 ? 8 : (dt == ZS_F32 ? 4 : 2); }
+
+// ---------------------------------------------------------------------------
+// Query executor: scratch + pinned staging for one stream of batches.
+// ---------------------------------------------------------------------------
+QueryExec::~QueryExec() { release(); }
+
+void QueryExec::release() {
+    auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
+    auto fh = [](void*& p) { if (p) cudaFreeHost(p); p = nullptr; };
+    if (done) { cudaEventSynchronize(done); cudaEventDestroy(done); done = nullptr; }
+    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C);
+    fh(h_blob);
+    cap_nq = 0;
+    cap_slabs = 0;
+}
+
+zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) {
+    const size_t ts = st.tsize;
+    const int64_t n = st.cfg.n, k = st.cfg.k;
+    if (nq <= cap_nq && nslab <= cap_slabs && kq <= cap_kq) return ZS_OK;
+    // grow geometrically
+    const int want_nq = std::max(nq, std::max(cap_nq * 3 / 2, 16));
+    const int64_t want_sl = std::max(nslab, std::max(cap_slabs * 3 / 2, (int64_t)64));
+    const int want_kq = std::max(kq, cap_kq);
+    if (done) cudaEventSynchronize(done);
+    release();
+    ZS_CU(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "event");
+    const size_t blob = sizeof(BatchHdr) + sizeof(QPlan) * want_nq + sizeof(int64_t) * (want_nq + 1) + 256;
+    ZS_CU(cudaMalloc(&d_blob, blob), "query plan buffer");
+    ZS_CU(cudaMallocHost(&h_blob, blob), "pinned plan buffer");
+    blob_bytes = blob;
+    auto al = [](void** p, size_t bytes, const char* what) -> zs_status {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(ZS_ENOMEM, "query scratch (%s): %s", what, cudaGetErrorString(e)); }
+        return ZS_OK;
+    };
+    zs_status s;
+    if ((s = al(&M, ts * want_sl * k * n, "stack")) != ZS_OK) return s;
+    if ((s = al(&G, ts * (size_t)want_nq * n * n, "gram")) != ZS_OK) return s;
+    if ((s = al(&sr, ts * (size_t)want_nq * want_kq, "sigma")) != ZS_OK) return s;
+    if ((s = al(&vr, ts * (size_t)want_nq * want_kq * n, "v")) != ZS_OK) return s;
+    if ((s = al(&tco, ts * (size_t)2 * want_nq * k * k, "partial")) != ZS_OK) return s;
+    if ((s = al(&C, ts * want_sl * k * want_kq, "lift coeff")) != ZS_OK) return s;
+    cap_nq = want_nq;
+    cap_slabs = want_sl;
+    cap_kq = want_kq;
+    return ZS_OK;
+}
+
+size_t QueryExec::bytes_for(const zs_store& st, int nq, int64_t nslab, int kq) {
+    const size_t ts = st.tsize;
+    const size_t n = st.cfg.n, k = st.cfg.k;
+    return ts * (nslab * k * n + (size_t)nq * n * n + (size_t)nq * kq * (n + 1) + 2 * (size_t)nq * k * k +
+                 nslab * k * kq) + sizeof(QPlan) * nq;
+}
+
+// ---------------------------------------------------------------------------
+// Planning (Algorithm 3, first steps; reading R1: 0-based inclusive ranges).
+// ---------------------------------------------------------------------------
+zs_status plan_queries(const zs_store& st, int64_t Trows, const int64_t* ts, const int64_t* te, int nq,
+                       int kq, std::vector<QPlan>& plans, std::vector<int64_t>& prefix) {
+    const int64_t b = st.cfg.b, n = st.cfg.n, k = st.cfg.k;
+    plans.resize(nq);
+    prefix.resize(nq + 1);
+    int64_t slab = 0;
+    for (int q = 0; q < nq; ++q) {
+        if (ts[q] < 0 || ts[q] > te[q] || te[q] >= Trows)
+            return fail(ZS_ERANGE, "query %d: range [%lld, %lld] outside [0, %lld)", q, (long long)ts[q],
+                        (long long)te[q], (long long)Trows);
+        QPlan& P = plans[q];
+        memset(&P, 0, sizeof P);
+        P.ts = ts[q];
+        P.te = te[q];
+        P.S = (int32_t)(ts[q] / b);
+        P.E = (int32_t)(te[q] / b);
+        P.nslab = P.E - P.S + 1;
+        P.slab0 = slab;
+        prefix[q] = slab;
+        slab += P.nslab;
+        // structural rank of the stacked matrix: sum of slab ranks
+        auto rows_of = [&](int64_t i) { return std::min<int64_t>(b, Trows - i * b); };
+        auto ki = [&](int64_t i) { return std::min<int64_t>(k, std::min<int64_t>(rows_of(i), n)); };
+        int64_t reff;
+        if (P.nslab == 1) {
+            reff = std::min<int64_t>(te[q] - ts[q] + 1, ki(P.S));
+        } else {
+            const int64_t rS = rows_of(P.S) - (ts[q] - (int64_t)P.S * b);
+            const int64_t rE = te[q] - (int64_t)P.E * b + 1;
+            reff = std::min(rS, ki(P.S)) + std::min(rE, ki(P.E)) + (int64_t)(P.nslab - 2) * ki(P.S + 1);
+        }
+        P.kcap = (int32_t)std::min<int64_t>(kq, reff);
+    }
+    prefix[nq] = slab;
+    return ZS_OK;
+}
+
+// Run one planned batch on `stream` with executor `x`.  Results go to the
+// buffers recorded in plans.
+zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan>& plans,
+                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream) {
+    const int nq = (int)plans.size();
+    const int64_t nslab = prefix[nq];
+    zs_status s = x.reserve(st, nq, nslab, kq);
+    if (s != ZS_OK) return s;
+    // the pinned plan buffer may still be read by the previous batch's copy
+    ZS_CU(cudaEventSynchronize(x.done), "plan buffer wait");
+    char* hb = (char*)x.h_blob;
+    BatchHdr* hh = (BatchHdr*)hb;
+    hh->nq = nq;
+    hh->pad = 0;
+    hh->nslab_total = nslab;
+    hh->T = Trows;
+    const size_t o_plans = (sizeof(BatchHdr) + 15) & ~size_t(15);
+    const size_t o_pref = o_plans + sizeof(QPlan) * nq;
+    memcpy(hb + o_plans, plans.data(), sizeof(QPlan) * nq);
+    memcpy(hb + o_pref, prefix.data(), sizeof(int64_t) * (nq + 1));
+    const size_t bytes = o_pref + sizeof(int64_t) * (nq + 1);
+    ZS_CU(cudaMemcpyAsync(x.d_blob, x.h_blob, bytes, cudaMemcpyHostToDevice, stream), "plan upload");
+    QueryArgs a;
+    memset(&a, 0, sizeof a);
+    char* db = (char*)x.d_blob;
+    a.hdr = (const BatchHdr*)db;
+    a.plans = (const QPlan*)(db + o_plans);
+    a.slab_prefix = (const int64_t*)(db + o_pref);
+    a.U = st.U;
+    a.sig = st.sig;
+    a.vt = st.vt;
+    a.b = (int32_t)st.cfg.b;
+    a.n = (int32_t)st.cfg.n;
+    a.k = st.cfg.k;
+    a.kq = kq;
+    a.kout = kout;
+    a.fp64_refine = (st.cfg.flags & ZS_FLAG_FP64_REFINE) ? 1 : 0;
+    a.M = x.M;
+    a.G = x.G;
+    a.sr = x.sr;
+    a.vr = x.vr;
+    a.tco = x.tco;
+    a.C = x.C;
+    cudaError_t e = launch_query(a, st.fp64, nq, nslab, st.tune, st.num_sms, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "query kernels");
+    ZS_CU(cudaEventRecord(x.done, stream), "event record");
+    return ZS_OK;
+}
+
+}  // namespace zs
+
+using namespace zs;
+
+// ---------------------------------------------------------------------------
+// Store lifetime.
+// ---------------------------------------------------------------------------
+static zs_status store_alloc(zs_store* st) {
+    const zs_store_config& c = st->cfg;
+    const size_t ts = st->tsize;
+    st->cap_blocks = (c.capacity_rows + c.b - 1) / c.b;
+    const size_t nb = (size_t)std::max<int64_t>(st->cap_blocks, 1);
+    auto al = [&](void** p, size_t bytes, const char* what) -> zs_status {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(ZS_ENOMEM, "%s (%zu bytes): %s", what, bytes, cudaGetErrorString(e)); }
+        return ZS_OK;
+    };
+    zs_status s;
+    if ((s = al(&st->U, ts * nb * c.b * c.k, "store U")) != ZS_OK) return s;
+    if ((s = al(&st->sig, ts * nb * c.k, "store sigma")) != ZS_OK) return s;
+    if ((s = al(&st->vt, ts * nb * c.k * c.n, "store V")) != ZS_OK) return s;
+    if ((s = al(&st->tail, st->insize * (size_t)c.b * c.n, "open-block rows")) != ZS_OK) return s;
+    // Gram scratch: chunk of blocks whose n x n Grams stay L2-sized
+    const size_t gper = ts * (size_t)c.n * c.n;
+    st->gchunk = (int)std::max<size_t>(1, std::min<size_t>(st->gram_budget / gper, 65535));
+    if ((s = al(&st->gscr, gper * st->gchunk, "gram scratch")) != ZS_OK) return s;
+    // host staging: two device buffers of whole blocks
+    const size_t blk_bytes = st->insize * (size_t)c.b * c.n;
+    st->stage_blocks = (int)std::max<size_t>(1, std::min<size_t>(st->stage_budget / blk_bytes, st->gchunk));
+    for (int i = 0; i < 2; ++i)
+        if ((s = al(&st->stage[i], blk_bytes * st->stage_blocks, "host staging")) != ZS_OK) return s;
+    ZS_CU(cudaMemset(st->U, 0, ts * nb * c.b * c.k), "memset");
+    ZS_CU(cudaMemset(st->sig, 0, ts * nb * c.k), "memset");
+    ZS_CU(cudaMemset(st->vt, 0, ts * nb * c.k * c.n), "memset");
+    ZS_CU(cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking), "stream");
+    for (int i = 0; i < 2; ++i) {
+        ZS_CU(cudaEventCreateWithFlags(&st->stage_free[i], cudaEventDisableTiming), "event");
+        ZS_CU(cudaEventCreateWithFlags(&st->stage_full[i], cudaEventDisableTiming), "event");
+        ZS_CU(cudaEventRecord(st->stage_free[i], st->copy_stream), "event");
+    }
+    ZS_CU(cudaEventCreateWithFlags(&st->append_done, cudaEventDisableTiming), "event");
+    ZS_CU(cudaEventCreateWithFlags(&st->entry, cudaEventDisableTiming), "event");
+    ZS_CU(cudaEventRecord(st->append_done, st->copy_stream), "event");
+    ZS_CU(cudaDeviceSynchronize(), "store init");
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_create(const zs_store_config* cfg, zs_store** out) {
+    if (!cfg || !out) return fail(ZS_EINVAL, "null argument");
+    *out = nullptr;
+    const zs_store_config& c = *cfg;
+    if (c.in_dtype != ZS_F64 && c.in_dtype != ZS_F32 && c.in_dtype != ZS_BF16)
+        return fail(ZS_EDTYPE, "unknown in_dtype %d", c.in_dtype);
+    if (c.n < 1 || c.n > 1024 || c.b < 1 || c.k < 1 || c.k > 64 || c.k > c.n || c.capacity_rows < 1 ||
+        c.b > (int64_t)1 << 24)
+        return fail(ZS_EINVAL, "bad store config (n=%lld b=%lld k=%d capacity=%lld)", (long long)c.n,
+                    (long long)c.b, c.k, (long long)c.capacity_rows);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return fail(ZS_ECUDA, "device %d not available", c.device);
+    }
+    const bool fp64 = (c.in_dtype == ZS_F64);
+    const bool ref = (c.flags & ZS_FLAG_FP64_REFINE) && !fp64;
+    if (eig_subspace_width((int)c.n, c.k, 16, fp64, ref) < 0)
+        return fail(ZS_EINVAL, "n=%lld with k=%d does not fit the eigen core's shared memory", (long long)c.n, c.k);
+    DeviceGuard g(c.device);
+    zs_store* st = new zs_store();
+    st->cfg = c;
+    st->fp64 = fp64;
+    st->tsize = fp64 ? 8 : 4;
+    st->insize = in_size(c.in_dtype);
+    cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    zs_status s = store_alloc(st);
+    if (s != ZS_OK) {
+        zs_store_destroy(st);
+        return s;
+    }
+    *out = st;
+    return ZS_OK;
+}
+
+extern "C" void zs_store_destroy(zs_store* st) {
+    if (!st) return;
+    DeviceGuard g(st->cfg.device);
+    if (st->copy_stream) cudaStreamSynchronize(st->copy_stream);
+    cudaDeviceSynchronize();
+    st->qx.release();
+    auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
+    f(st->U); f(st->sig); f(st->vt); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]);
+    for (int i = 0; i < 2; ++i) {
+        if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
+        if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
+    }
+    if (st->append_done) cudaEventDestroy(st->append_done);
+    if (st->entry) cudaEventDestroy(st->entry);
+    if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
+    delete st;
+}
+
+// ---------------------------------------------------------------------------
+// Storage phase.
+// ---------------------------------------------------------------------------
+static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64_t rows_total, int nblk,
+                                 int64_t slot0, cudaStream_t stream) {
+    const zs_store_config& c = st->cfg;
+    for (int j0 = 0; j0 < nblk; j0 += st->gchunk) {
+        const int nb = std::min(st->gchunk, nblk - j0);
+        CompressChunk ch;
+        memset(&ch, 0, sizeof ch);
+        ch.A = (const char*)A + (size_t)j0 * c.b * lda * st->insize;
+        ch.lda = lda;
+        ch.rows_total = std::min<int64_t>(rows_total - (int64_t)j0 * c.b, (int64_t)nb * c.b);
+        ch.nblk = nb;
+        ch.slot0 = (int32_t)(slot0 + j0);
+        ch.b = (int32_t)c.b;
+        ch.n = (int32_t)c.n;
+        ch.k = c.k;
+        ch.in_kind = c.in_dtype;
+        ch.G = st->gscr;
+        ch.U = st->U;
+        ch.sig = st->sig;
+        ch.vt = st->vt;
+        cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "compression kernels");
+    }
+    return ZS_OK;
+}
+
+// copy `rows` rows (stride ld elements) from src to dst (stride n), either side
+static zs_status copy_rows(zs_store* st, void* dst, const void* src, int64_t rows, int64_t ld, bool src_dev,
+                           cudaStream_t s) {
+    if (rows <= 0) return ZS_OK;
+    const size_t es = st->insize;
+    const size_t w = es * st->cfg.n;
+    ZS_CU(cudaMemcpy2DAsync(dst, w, src, es * ld, w, rows, src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+          "row copy");
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nrows, int64_t ld,
+                                     int32_t rows_on_device, void* stream_) {
+    if (!st) return fail(ZS_EINVAL, "null store");
+    if (nrows == 0) return ZS_OK;
+    if (!rows || nrows < 0 || ld < st->cfg.n) return fail(ZS_EINVAL, "bad rows/nrows/ld");
+    std::lock_guard<std::mutex> lk(st->mu);
+    const zs_store_config& c = st->cfg;
+    if (st->T + nrows > st->cap_blocks * c.b)
+        return fail(ZS_ENOMEM, "append of %lld rows exceeds capacity %lld", (long long)nrows,
+                    (long long)(st->cap_blocks * c.b));
+    DeviceGuard g(c.device);
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const bool dev = rows_on_device != 0;
+    const size_t es = st->insize;
+    const int64_t b = c.b;
+    int64_t pos = 0;
+    int64_t T = st->T;
+    zs_status s;
+    // device rows may still be being written on the caller's stream
+    ZS_CU(cudaEventRecord(st->entry, stream), "event");
+    ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->entry, 0), "wait");
+    // (1) extend the open block
+    const int64_t tail_rows = T % b;
+    if (tail_rows > 0) {
+        const int64_t f = std::min(b - tail_rows, nrows);
+        ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->append_done, 0), "wait");
+        if ((s = copy_rows(st, (char*)st->tail + es * tail_rows * c.n, rows, f, ld, dev, st->copy_stream)) != ZS_OK)
+            return s;
+        ZS_CU(cudaEventRecord(st->stage_full[0], st->copy_stream), "event");
+        ZS_CU(cudaStreamWaitEvent(stream, st->stage_full[0], 0), "wait");
+        if ((s = compress_blocks(st, st->tail, c.n, tail_rows + f, 1, T / b, stream)) != ZS_OK) return s;
+        pos = f;
+        T += f;
+    }
+    // (2) whole blocks
+    const int64_t full = (nrows - pos) / b;
+    if (full > 0) {
+        const char* src = (const char*)rows + es * pos * ld;
+        if (dev) {
+            if ((s = compress_blocks(st, src, ld, full * b, (int)full, T / b, stream)) != ZS_OK) return s;
+        } else {
+            int which = 0;
+            for (int64_t j = 0; j < full; j += st->stage_blocks, which ^= 1) {
+                const int64_t nb = std::min<int64_t>(st->stage_blocks, full - j);
+                ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->stage_free[which], 0), "wait");
+                if ((s = copy_rows(st, st->stage[which], src + es * j * b * ld, nb * b, ld, false, st->copy_stream)) != ZS_OK)
+                    return s;
+                ZS_CU(cudaEventRecord(st->stage_full[which], st->copy_stream), "event");
+                ZS_CU(cudaStreamWaitEvent(stream, st->stage_full[which], 0), "wait");
+                if ((s = compress_blocks(st, st->stage[which], c.n, nb * b, (int)nb, (T + j * b) / b, stream)) != ZS_OK)
+                    return s;
+                ZS_CU(cudaEventRecord(st->stage_free[which], stream), "event");
+            }
+        }
+        pos += full * b;
+        T += full * b;
+    }
+    // (3) rows of a new open block
+    const int64_t rem = nrows - pos;
+    if (rem > 0) {
+        ZS_CU(cudaEventRecord(st->append_done, stream), "event");   // tail no longer read
+        ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->append_done, 0), "wait");
+        if ((s = copy_rows(st, st->tail, (const char*)rows + es * pos * ld, rem, ld, dev, st->copy_stream)) != ZS_OK)
+            return s;
+        ZS_CU(cudaEventRecord(st->stage_full[0], st->copy_stream), "event");
+        ZS_CU(cudaStreamWaitEvent(stream, st->stage_full[0], 0), "wait");
+        if ((s = compress_blocks(st, st->tail, c.n, rem, 1, T / b, stream)) != ZS_OK) return s;
+        T += rem;
+    }
+    ZS_CU(cudaEventRecord(st->append_done, stream), "event");
+    // host rows are free to reuse once the copies have run
+    if (!dev) ZS_CU(cudaStreamSynchronize(st->copy_stream), "host copy");
+    st->T = T;
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks, int64_t* bytes) {
+    if (!st) return fail(ZS_EINVAL, "null store");
+    const int64_t T = st->T, b = st->cfg.b;
+    const int64_t nb = (T + b - 1) / b;
+    if (rows) *rows = T;
+    if (nblocks) *nblocks = nb;
+    if (bytes) *bytes = nb * (b * st->cfg.k + st->cfg.k + st->cfg.k * st->cfg.n) * st->tsize;
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_export_block(const zs_store* st_, int64_t i, void* U, void* sigma, void* Vt,
+                                           int32_t* rows_i, int32_t* k_i, void* stream_) {
+    zs_store* st = const_cast<zs_store*>(st_);
+    if (!st) return fail(ZS_EINVAL, "null store");
+    std::lock_guard<std::mutex> lk(st->mu);
+    const int64_t T = st->T, b = st->cfg.b, n = st->cfg.n, k = st->cfg.k;
+    const int64_t nb = (T + b - 1) / b;
+    if (i < 0 || i >= nb) return fail(ZS_ENOTFOUND, "block %lld not in [0, %lld)", (long long)i, (long long)nb);
+    DeviceGuard g(st->cfg.device);
+    cudaStream_t s = (cudaStream_t)stream_;
+    ZS_CU(cudaStreamWaitEvent(s, st->append_done, 0), "wait");
+    const int64_t r = std::min(b, T - i * b);
+    const size_t ts = st->tsize;
+    if (U) ZS_CU(cudaMemcpyAsync(U, (char*)st->U + ts * i * b * k, ts * r * k, cudaMemcpyDeviceToDevice, s), "copy");
+    if (sigma) ZS_CU(cudaMemcpyAsync(sigma, (char*)st->sig + ts * i * k, ts * k, cudaMemcpyDeviceToDevice, s), "copy");
+    if (Vt) ZS_CU(cudaMemcpyAsync(Vt, (char*)st->vt + ts * i * k * n, ts * k * n, cudaMemcpyDeviceToDevice, s), "copy");
+    if (rows_i) *rows_i = (int32_t)r;
+    if (k_i) *k_i = (int32_t)std::min<int64_t>(k, std::min<int64_t>(r, n));
+    return ZS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Query phase.
+// ---------------------------------------------------------------------------
+namespace zs {
+zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, const int64_t* te, int nq, int kout,
+                             const zs_result* res, cudaStream_t stream, int64_t Trows) {
+    const int kq = std::min<int>(kout, (int)st->cfg.n);
+    std::vector<QPlan> plans;
+    std::vector<int64_t> prefix;
+    zs_status s = plan_queries(*st, Trows, ts, te, nq, kq, plans, prefix);
+    if (s != ZS_OK) return s;
+    for (int q = 0; q < nq; ++q) {
+        const zs_result& r = res[q];
+        if (!r.U || !r.S || !r.V || r.ldu < kout || r.ldv < kout)
+            return fail(ZS_EINVAL, "query %d: bad result buffers", q);
+        plans[q].U = r.U;
+        plans[q].ldu = r.ldu;
+        plans[q].S_out = r.S;
+        plans[q].V_out = r.V;
+        plans[q].ldv = r.ldv;
+        plans[q].rank = r.rank;
+    }
+    ZS_CU(cudaStreamWaitEvent(stream, st->append_done, 0), "wait for appends");
+    // the executor's scratch may still be in use by a batch on another stream
+    if (x.done) ZS_CU(cudaStreamWaitEvent(stream, x.done, 0), "wait for previous batch");
+    // split batches whose scratch would exceed the budget
+    int q0 = 0;
+    while (q0 < nq) {
+        int q1 = q0;
+        int64_t sl = 0;
+        while (q1 < nq) {
+            const int64_t add = plans[q1].nslab;
+            if (q1 > q0 && QueryExec::bytes_for(*st, q1 - q0 + 1, sl + add, kq) > st->query_budget) break;
+            sl += add;
+            ++q1;
+        }
+        std::vector<QPlan> sub(plans.begin() + q0, plans.begin() + q1);
+        std::vector<int64_t> pre(q1 - q0 + 1);
+        int64_t base = sub[0].slab0;
+        for (int q = 0; q < q1 - q0; ++q) {
+            sub[q].slab0 -= base;
+            pre[q] = sub[q].slab0;
+        }
+        pre[q1 - q0] = sl;
+        if ((s = run_batch(*st, x, Trows, sub, pre, kq, kout, stream)) != ZS_OK) return s;
+        q0 = q1;
+    }
+    return ZS_OK;
+}
+}  // namespace zs
+
+extern "C" zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq, int32_t k_out,
+                                    const zs_result* results, void* stream) {
+    if (!st || !ts || !te || !results || nq < 0) return fail(ZS_EINVAL, "null argument");
+    if (nq == 0) return ZS_OK;
+    if (k_out < 1 || k_out > 64) return fail(ZS_EINVAL, "k_out %d not in 1..64", k_out);
+    std::lock_guard<std::mutex> lk(st->mu);
+    DeviceGuard g(st->cfg.device);
+    return query_batch_locked(st, st->qx, ts, te, nq, k_out, results, (cudaStream_t)stream, st->T);
+}
+
+extern "C" zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out, const zs_result* res,
+                              void* stream) {
+    if (!res) return fail(ZS_EINVAL, "null result");
+    return zs_query_batch(st, &t_s, &t_e, 1, k_out, res, stream);
+}
+
+extern "C" const char* zs_status_str(zs_status s) {
+    switch (s) {
+        case ZS_OK: return "ok";
+        case ZS_EINVAL: return "invalid argument";
+        case ZS_ERANGE: return "range out of bounds";
+        case ZS_ENOMEM: return "out of memory";
+        case ZS_EBUSY: return "busy";
+        case ZS_ETIMEDOUT: return "timed out";
+        case ZS_EDTYPE: return "unsupported dtype";
+        case ZS_ECUDA: return "CUDA error";
+        case ZS_EINTERNAL: return "internal error";
+        case ZS_ENOTFOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* zs_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int64_t zs_launch_count(void) { return launch_count_total(); }

@@ -1,0 +1,69 @@
+// zs_api_internal.h - host-side store and executor types shared by zs_api.cu
+// and zs_serve.cpp.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <vector>
+
+#include "zoomsvd.h"
+#include "zs_internal.h"
+
+namespace zs {
+
+// Scratch and pinned plan staging for one stream of query batches.
+struct QueryExec {
+    int cap_nq = 0;
+    int64_t cap_slabs = 0;
+    int cap_kq = 0;
+    void* d_blob = nullptr;       // BatchHdr | QPlan[] | prefix[]
+    void* h_blob = nullptr;       // pinned mirror
+    size_t blob_bytes = 0;
+    void *M = nullptr, *G = nullptr, *sr = nullptr, *vr = nullptr, *tco = nullptr, *C = nullptr;
+    cudaEvent_t done = nullptr;   // last batch that used this scratch
+    ~QueryExec();
+    void release();
+    zs_status reserve(const zs_store& st, int nq, int64_t nslab, int kq);
+    static size_t bytes_for(const zs_store& st, int nq, int64_t nslab, int kq);
+};
+
+zs_status fail(zs_status s, const char* fmt, ...);
+zs_status cuda_fail(cudaError_t e, const char* what);
+zs_status plan_queries(const zs_store& st, int64_t Trows, const int64_t* ts, const int64_t* te, int nq, int kq,
+                       std::vector<QPlan>& plans, std::vector<int64_t>& prefix);
+zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan>& plans,
+                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream);
+zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, const int64_t* te, int nq, int kout,
+                             const zs_result* res, cudaStream_t stream, int64_t Trows);
+
+}  // namespace zs
+
+struct zs_store {
+    zs_store_config cfg;
+    bool fp64 = false;
+    int tsize = 4;                 // factor element bytes
+    int insize = 4;                // input element bytes
+    int num_sms = 1;
+    int64_t T = 0;                 // rows appended (published)
+    int64_t cap_blocks = 0;
+    void* U = nullptr;             // cap_blocks x b x k
+    void* sig = nullptr;           // cap_blocks x k
+    void* vt = nullptr;            // cap_blocks x k x n
+    void* tail = nullptr;          // b x n raw rows of the open block
+    void* gscr = nullptr;          // gchunk x n x n Gram scratch
+    int gchunk = 1;
+    size_t gram_budget = (size_t)64 << 20;
+    void* stage[2] = {nullptr, nullptr};
+    int stage_blocks = 1;
+    size_t stage_budget = (size_t)64 << 20;
+    size_t query_budget = (size_t)8 << 30;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_free[2] = {nullptr, nullptr};
+    cudaEvent_t stage_full[2] = {nullptr, nullptr};
+    cudaEvent_t append_done = nullptr;
+    cudaEvent_t entry = nullptr;
+    std::mutex mu;
+    zs::Tuning tune;
+    zs::QueryExec qx;
+};

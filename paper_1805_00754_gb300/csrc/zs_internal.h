@@ -1,0 +1,104 @@
+// zs_internal.h - structures shared by the kernels (zs_kernels.cu) and the host
+// runtime (zs_api.cu, zs_serve.cpp).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace zs {
+
+enum InKind { IN_F64 = 0, IN_F32 = 1, IN_BF16 = 2 };
+
+// Singular values at or below this fraction of sigma_1 are reported as zero
+// (their U/V columns are zero and rank_out excludes them).
+constexpr double kRankTolF64 = 1e-13;
+constexpr float kRankTolF32 = 1e-7f;
+
+// One storage-phase launch covers `nblk` consecutive blocks of b rows that start
+// at row 0 of `A` (row stride lda, element type in_kind); the last of them may
+// be short (rows_total - (nblk-1)*b rows).  Their factors go to store slots
+// slot0 .. slot0+nblk-1.  G is scratch for nblk n x n Gram matrices.
+struct CompressChunk {
+    const void* A;
+    int64_t lda;
+    int64_t rows_total;
+    int32_t nblk;
+    int32_t slot0;
+    int32_t b;
+    int32_t n;
+    int32_t k;
+    int32_t in_kind;
+    void* G;          // nblk * n * n accumulator type
+    void* U;          // store: slot-major, b * k per slot
+    void* sig;        // store: k per slot
+    void* vt;         // store: k * n per slot
+};
+
+// Per-query plan of a batch (host-computed, then copied to the device).
+// Reading R1: rows are 0-based, ranges inclusive; S = t_s / b, E = t_e / b.
+struct QPlan {
+    int64_t ts, te;
+    int32_t S, E;
+    int32_t nslab;        // E - S + 1 slabs of k rows in the stacked matrix M
+    int32_t kcap;         // min(kq, structural rank of M)
+    int64_t slab0;        // global index of this query's first slab
+    void* U;              // result buffers (caller device memory)
+    int64_t ldu;
+    void* S_out;
+    void* V_out;
+    int64_t ldv;
+    int32_t* rank;
+    int32_t pad0, pad1;
+};
+
+// Header of a query batch, read by the kernels from device memory so that one
+// set of persistent launches (and one captured graph) serves any batch shape
+// up to the executor's capacity.
+struct BatchHdr {
+    int32_t nq;
+    int32_t pad;
+    int64_t nslab_total;
+    int64_t T;            // rows in the store when the batch was planned
+};
+
+// Device pointers of a store and its query scratch, passed by value.
+struct QueryArgs {
+    const BatchHdr* hdr;
+    const QPlan* plans;
+    const int64_t* slab_prefix;   // nq + 1 entries: plans[q].slab0, then total
+    // store
+    const void* U;
+    const void* sig;
+    const void* vt;
+    int32_t b, n, k;
+    int32_t kq;                   // eigenpairs computed per query (= min(k_out, n))
+    int32_t kout;
+    int32_t fp64_refine;
+    // scratch
+    void* M;          // nslab_total * k * n     stacked Sigma_i V_i^T
+    void* G;          // nq * n * n              Gram of M
+    void* sr;         // nq * kq                 stitched singular values
+    void* vr;         // nq * kq * n             stitched right vectors (transposed)
+    void* tco;        // 2 * nq * k * k          Partial-SVD lift coefficients
+    void* C;          // nslab_total * k * kq    lift coefficients per slab
+};
+
+// Launch configuration chosen by the autotuner (or defaults).
+struct Tuning {
+    int gram_threads = 256;
+    int lift_rows = 64;          // rows staged per lift tile
+    int slab_ctas_per_sm = 4;    // persistent grid for slab work lists
+    int eig_m_extra = 16;        // subspace oversampling p (m = kq + p)
+};
+
+// Launchers (zs_kernels.cu).  All enqueue on `st` and return cudaError_t of the
+// launch.  `fp64` selects the double-precision instantiation (F64 store).
+cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu,
+                            int num_sms, cudaStream_t st);
+cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs,
+                         const Tuning& tu, int num_sms, cudaStream_t st);
+int eig_subspace_width(int n, int kq, int extra, bool fp64, bool refine);
+size_t eig_smem_bytes(int n, int m, bool fp64, bool refine);
+void note_launches(int64_t n);
+
+}  // namespace zs

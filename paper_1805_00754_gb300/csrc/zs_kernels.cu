@@ -1,0 +1,945 @@
+// zs_kernels.cu - sm_103a kernels of the range-SVD hot path.
+//
+// Storage phase (Section 3.2, Algorithm 1; one launch set per chunk of blocks):
+//   k_gram_compress   G_i = A_i^T A_i for every block (symmetric tiles)
+//   k_eig_compress    top-k eigenpairs of G_i -> sigma_i, V_i (Section 2.1)
+//   k_form_u          U_i = A_i V_i Sigma_i^{-1}
+// Query phase (Section 3.3; persistent work-list kernels over a batch):
+//   k_partial         Partial-SVD of the boundary blocks (Algorithm 3, Eq. 5-6)
+//   k_stack           stack Sigma_i V_i^T of the interior blocks (Algorithm 2)
+//   k_gram_query      M^T M of the stacked matrix
+//   k_eig_query       top-k_q eigenpairs -> Sigma_r, V_r (Algorithm 2)
+//   k_ur              U_r = M V_r Sigma_r^{-1} and the per-slab lift
+//                     coefficients (Partial-SVD slabs folded with their Sigma V~ Sigma~^-1)
+//   k_lift            U_{S:E} = diag(S:E) U_r block by block (Eq. 9)
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <atomic>
+#include <type_traits>
+
+#include "zs_internal.h"
+#include "zs_linalg.cuh"
+
+namespace zs {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int64_t n) { g_launches += n; }
+int64_t launch_count_total() { return g_launches.load(); }
+
+__device__ __forceinline__ double ld_in(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_in(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_in(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(reinterpret_cast<const __nv_bfloat16*>(p)));
+}
+
+template <typename T, bool REF> struct Prec { using TR = T; };
+template <> struct Prec<float, true> { using TR = double; };
+
+// ---------------------------------------------------------------------------
+// Gram tiles: G[I0:I0+64, J0:J0+64] (and its mirror) of rows x n matrix A.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tile_pair(int p, int ntile, int& ti, int& tj) {
+    ti = 0;
+    while (p >= ntile - ti) { p -= ntile - ti; ++ti; }
+    tj = ti + p;
+}
+
+template <typename Tin, typename T>
+__device__ void gram_tile(const Tin* __restrict__ A, int64_t lda, int rows, int n,
+                          T* __restrict__ G, int ti, int tj, T (*As)[64], T (*Bs)[64]) {
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int I0 = ti * 64, J0 = tj * 64;
+    const bool diag = (ti == tj);
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int r0 = 0; r0 < rows; r0 += 32) {
+        for (int e = tid; e < 32 * 64; e += 256) {
+            const int r = e >> 6, c = e & 63, gr = r0 + r;
+            const bool rv = gr < rows;
+            As[r][c] = (rv && I0 + c < n) ? T(ld_in(A + (int64_t)gr * lda + I0 + c)) : T(0);
+            if (!diag) Bs[r][c] = (rv && J0 + c < n) ? T(ld_in(A + (int64_t)gr * lda + J0 + c)) : T(0);
+        }
+        __syncthreads();
+        const T(*Bp)[64] = diag ? As : Bs;
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            T a[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[r][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bp[r][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bv[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int row = I0 + ty + 16 * i, col = J0 + tx + 16 * j;
+            if (row < n && col < n) {
+                G[(int64_t)row * n + col] = acc[i][j];
+                if (!diag) G[(int64_t)col * n + row] = acc[i][j];
+            }
+        }
+}
+
+template <typename Tin, typename T>
+__global__ void __launch_bounds__(256) k_gram_compress(CompressChunk c) {
+    __shared__ __align__(16) T As[32][64];
+    __shared__ __align__(16) T Bs[32][64];
+    const int ntile = (c.n + 63) / 64;
+    int ti, tj;
+    tile_pair(blockIdx.x, ntile, ti, tj);
+    for (int j = blockIdx.y; j < c.nblk; j += gridDim.y) {
+        const int64_t r0 = (int64_t)j * c.b;
+        const int rows = (int)min((int64_t)c.b, c.rows_total - r0);
+        gram_tile<Tin, T>((const Tin*)c.A + r0 * c.lda, c.lda, rows, c.n,
+                          (T*)c.G + (int64_t)j * c.n * c.n, ti, tj, As, Bs);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_query(QueryArgs a) {
+    __shared__ __align__(16) T As[32][64];
+    __shared__ __align__(16) T Bs[32][64];
+    const int ntile = (a.n + 63) / 64;
+    int ti, tj;
+    tile_pair(blockIdx.x, ntile, ti, tj);
+    const int nq = a.hdr->nq;
+    for (int q = blockIdx.y; q < nq; q += gridDim.y) {
+        const QPlan& P = a.plans[q];
+        gram_tile<T, T>((const T*)a.M + P.slab0 * a.k * a.n, a.n, P.nslab * a.k, a.n,
+                        (T*)a.G + (int64_t)q * a.n * a.n, ti, tj, As, Bs);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Small symmetric eigenproblem with optional FP64 refinement.
+//   in : A_T (m x m, ld) in T; when REF also A_R (same matrix, double, ld)
+//   out: theta[c] descending (TR) and eigenvector c = column perm[c] of Zo
+// ---------------------------------------------------------------------------
+template <typename T, bool REF>
+struct SmallEig {
+    using TR = typename Prec<T, REF>::TR;
+    T* A_T;
+    T* Z_T;
+    double* A_R;   // REF only
+    double* X;     // REF only
+    double* W;     // REF only
+    int ld;
+};
+
+template <typename T, bool REF>
+__device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, JacobiScratch<double>& jd,
+                          typename Prec<T, REF>::TR* theta, int* perm, typename Prec<T, REF>::TR*& Zo) {
+    using TR = typename Prec<T, REF>::TR;
+    const int tid = threadIdx.x, nt = blockDim.x, ld = s.ld;
+    const int sweeps = std::is_same<T, double>::value ? 40 : 30;
+    jacobi_eig<T>(s.A_T, ld, s.Z_T, ld, m, js, sweeps, true);
+    if constexpr (REF) {
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, c = e - (e / m) * m;
+            double acc = 0;
+            for (int l = 0; l < m; ++l) acc += s.A_R[i * ld + l] * (double)s.Z_T[l * ld + c];
+            s.X[i * ld + c] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            const int a = e / m, c = e - (e / m) * m;
+            double acc = 0;
+            for (int i = 0; i < m; ++i) acc += (double)s.Z_T[i * ld + a] * s.X[i * ld + c];
+            s.A_R[a * ld + c] = acc;
+        }
+        __syncthreads();
+        jacobi_eig<double>(s.A_R, ld, s.W, ld, m, jd, 4, true);
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, c = e - (e / m) * m;
+            double acc = 0;
+            for (int a = 0; a < m; ++a) acc += (double)s.Z_T[i * ld + a] * s.W[a * ld + c];
+            s.X[i * ld + c] = acc;
+        }
+        __syncthreads();
+        sort_desc<double>(s.A_R, ld, m, perm);
+        for (int c = tid; c < m; c += nt) theta[c] = s.A_R[perm[c] * ld + perm[c]];
+        Zo = reinterpret_cast<TR*>(s.X);
+    } else {
+        sort_desc<T>(s.A_T, ld, m, perm);
+        for (int c = tid; c < m; c += nt) theta[c] = s.A_T[perm[c] * ld + perm[c]];
+        Zo = reinterpret_cast<TR*>(s.Z_T);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Top-kw eigenpairs of the symmetric PSD n x n matrix G (global, row-major).
+// Dense Jacobi when m == n (n <= 64); otherwise subspace iteration with
+// Rayleigh-Ritz on m columns started from the m columns of G with the largest
+// diagonal.  Output: theta[c] (c < kw) descending and the eigenvectors as
+// columns of V (n x kw, row stride ldv) in shared memory.
+// ---------------------------------------------------------------------------
+template <typename T, bool REF>
+struct EigWork {
+    T* Q;       // n x ldq
+    T* Y;       // n x ldq
+    int ldq;
+    SmallEig<T, REF> se;
+};
+
+template <typename T, bool REF>
+__device__ __forceinline__ size_t eig_carve(char* base, int n, int m, EigWork<T, REF>& w) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base + off; off += (bytes + 15) & ~size_t(15); return p; };
+    const bool dense = (m == n && n <= 64);
+    const int ld = m + 1;
+    w.ldq = ld;
+    if (dense) {
+        w.Q = nullptr;
+        w.Y = nullptr;
+    } else {
+        w.Q = (T*)take(sizeof(T) * (size_t)n * ld);
+        w.Y = (T*)take(sizeof(T) * (size_t)n * ld);
+    }
+    w.se.ld = ld;
+    w.se.A_T = (T*)take(sizeof(T) * (size_t)m * ld);
+    w.se.Z_T = (T*)take(sizeof(T) * (size_t)m * ld);
+    if (REF) {
+        w.se.A_R = (double*)take(sizeof(double) * (size_t)m * ld);
+        w.se.X = (double*)take(sizeof(double) * (size_t)m * ld);
+        w.se.W = (double*)take(sizeof(double) * (size_t)m * ld);
+    } else {
+        w.se.A_R = w.se.X = w.se.W = nullptr;
+    }
+    return off;
+}
+
+struct EigStatic {
+    int perm[ZS_MAXM];
+    double theta[ZS_MAXM];
+    double resid[ZS_MAXM];
+    double red[32];
+    double coef[ZS_MAXM];
+    int flag;
+};
+
+template <typename T, bool REF, int MB>
+__device__ void eig_solve(const T* __restrict__ G, int n, int m, int kw, EigWork<T, REF>& w,
+                          JacobiScratch<T>& js, JacobiScratch<double>& jd, EigStatic& es,
+                          T*& V, int& ldv) {
+    using TR = typename Prec<T, REF>::TR;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+    TR* theta = reinterpret_cast<TR*>(es.theta);
+    T* red = reinterpret_cast<T*>(es.red);
+    T* coef = reinterpret_cast<T*>(es.coef);
+    const int ld = w.se.ld;
+    TR* Zo;
+    if (m == n && n <= 64) {
+        // dense Jacobi on G itself
+        for (int e = tid; e < n * n; e += nt) {
+            const int i = e / n, j = e - (e / n) * n;
+            const T g = G[(int64_t)i * n + j];
+            w.se.A_T[i * ld + j] = g;
+            if (REF) w.se.A_R[i * ld + j] = (double)g;
+        }
+        __syncthreads();
+        small_eig<T, REF>(w.se, n, js, jd, theta, es.perm, Zo);
+        // selected eigenvectors -> columns of A_T (no longer needed)
+        for (int e = tid; e < n * kw; e += nt) {
+            const int i = e / kw, c = e - (e / kw) * kw;
+            w.se.A_T[i * ld + c] = (T)Zo[i * ld + es.perm[c]];
+        }
+        __syncthreads();
+        V = w.se.A_T;
+        ldv = ld;
+        return;
+    }
+    T* Q = w.Q;
+    T* Y = w.Y;
+    const int ldq = w.ldq;
+    // pivots: the m largest diagonal entries of G (stable on ties); diag in Y[0..n)
+    for (int i = tid; i < n; i += nt) Y[i] = G[(int64_t)i * n + i];
+    __syncthreads();
+    for (int i = tid; i < n; i += nt) {
+        const T v = Y[i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const T u = Y[j];
+            rk += (u > v) || (u == v && j < i);
+        }
+        if (rk < m) es.perm[rk] = i;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * m; e += nt) {
+        const int c = e / n, i = e - (e / n) * n;
+        Q[i * ldq + c] = G[(int64_t)es.perm[c] * n + i];     // column perm[c] of G (symmetric)
+    }
+    __syncthreads();
+    mgs_orth<T>(Q, ldq, n, m, red, coef);
+    const T tol_r = T(8) * eps_of<T>() * zsqrt(T(n));
+    const int maxit = std::is_same<T, double>::value ? 60 : 30;
+    for (int it = 0; it < maxit; ++it) {
+        // Y = G Q
+        for (int i = tid; i < n; i += nt) {
+            T acc[MB];
+#pragma unroll
+            for (int c = 0; c < MB; ++c) acc[c] = T(0);
+            for (int l = 0; l < n; ++l) {
+                const T g = G[(int64_t)l * n + i];
+                const T* qr = Q + l * ldq;
+#pragma unroll
+                for (int c = 0; c < MB; ++c)
+                    if (c < m) acc[c] += g * qr[c];
+            }
+#pragma unroll
+            for (int c = 0; c < MB; ++c)
+                if (c < m) Y[i * ldq + c] = acc[c];
+        }
+        __syncthreads();
+        // Rayleigh quotient  Q^T Y  (FP64-accumulated when REF)
+        for (int e = tid; e < m * m; e += nt) {
+            const int a = e / m, c = e - (e / m) * m;
+            if (c < a) continue;
+            TR acc = 0;
+            for (int i = 0; i < n; ++i) acc += (TR)Q[i * ldq + a] * (TR)Y[i * ldq + c];
+            w.se.A_T[a * ld + c] = (T)acc;
+            w.se.A_T[c * ld + a] = (T)acc;
+            if (REF) {
+                w.se.A_R[a * ld + c] = (double)acc;
+                w.se.A_R[c * ld + a] = (double)acc;
+            }
+        }
+        __syncthreads();
+        small_eig<T, REF>(w.se, m, js, jd, theta, es.perm, Zo);
+        // Ritz vectors in place: Q <- Q Z(:, perm), Y <- Y Z(:, perm)
+        for (int i = tid; i < n; i += nt) {
+            T row[MB];
+#pragma unroll
+            for (int a = 0; a < MB; ++a) row[a] = (a < m) ? Q[i * ldq + a] : T(0);
+            for (int c = 0; c < m; ++c) {
+                const TR* zc = Zo + es.perm[c];
+                TR acc = 0;
+#pragma unroll
+                for (int a = 0; a < MB; ++a)
+                    if (a < m) acc += (TR)row[a] * zc[a * ld];
+                Q[i * ldq + c] = (T)acc;
+            }
+#pragma unroll
+            for (int a = 0; a < MB; ++a) row[a] = (a < m) ? Y[i * ldq + a] : T(0);
+            for (int c = 0; c < m; ++c) {
+                const TR* zc = Zo + es.perm[c];
+                TR acc = 0;
+#pragma unroll
+                for (int a = 0; a < MB; ++a)
+                    if (a < m) acc += (TR)row[a] * zc[a * ld];
+                Y[i * ldq + c] = (T)acc;
+            }
+        }
+        __syncthreads();
+        // residuals of the wanted pairs
+        for (int c = wid; c < kw; c += nw) {
+            const T th = (T)theta[c];
+            T ss = 0;
+            for (int i = lane; i < n; i += 32) {
+                const T d = Y[i * ldq + c] - th * Q[i * ldq + c];
+                ss += d * d;
+            }
+            ss = warp_sum(ss);
+            if (lane == 0) es.resid[c] = (double)zsqrt(ss);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double mx = 0;
+            for (int c = 0; c < kw; ++c) mx = fmax(mx, es.resid[c]);
+            const double th0 = (double)theta[0];
+            es.flag = (th0 <= 0.0) || (mx <= (double)tol_r * th0);
+        }
+        __syncthreads();
+        const int done = es.flag;
+        __syncthreads();
+        if (done || it == maxit - 1) break;
+        // next block: orthonormalised Ritz-rotated G Q
+        T* t = Q;
+        Q = Y;
+        Y = t;
+        mgs_orth<T>(Q, ldq, n, m, red, coef);
+    }
+    V = Q;
+    ldv = ldq;
+}
+
+// Make the largest-|.| entry of each column positive (lowest index on ties).
+template <typename T>
+__device__ void canon_signs(T* V, int ldv, int n, int kw, int* sgn) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int c = wid; c < kw; c += nw) {
+        T best = T(-1);
+        int bi = 0x7fffffff;
+        for (int i = lane; i < n; i += 32) {
+            const T v = zabs(V[i * ldv + c]);
+            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) sgn[c] = (bi < n && V[bi * ldv + c] < T(0)) ? -1 : 1;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T rank_tol();
+template <> __device__ __forceinline__ float rank_tol<float>() { return kRankTolF32; }
+template <> __device__ __forceinline__ double rank_tol<double>() { return kRankTolF64; }
+
+// ---------------------------------------------------------------------------
+// Storage phase: eigen-core per block, then U = A V Sigma^-1.
+// ---------------------------------------------------------------------------
+template <typename T, bool REF, int MB>
+__global__ void __launch_bounds__(256) k_eig_compress(CompressChunk c, int m) {
+    extern __shared__ __align__(16) char dsm[];
+    __shared__ JacobiScratch<T> js;
+    __shared__ JacobiScratch<double> jd;
+    __shared__ EigStatic es;
+    __shared__ int sgn[ZS_MAXM];
+    EigWork<T, REF> w;
+    eig_carve<T, REF>(dsm, c.n, m, w);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = blockIdx.x; j < c.nblk; j += gridDim.x) {
+        const int64_t r0 = (int64_t)j * c.b;
+        const int rows = (int)min((int64_t)c.b, c.rows_total - r0);
+        const int kcap = min(c.k, min(rows, c.n));
+        T* V;
+        int ldv;
+        eig_solve<T, REF, MB>((const T*)c.G + (int64_t)j * c.n * c.n, c.n, m, c.k, w, js, jd, es, V, ldv);
+        canon_signs<T>(V, ldv, c.n, c.k, sgn);
+        using TR = typename Prec<T, REF>::TR;
+        const TR* theta = reinterpret_cast<const TR*>(es.theta);
+        const T s0 = zsqrt((T)fmax((double)theta[0], 0.0));
+        const int slot = c.slot0 + j;
+        T* sig = (T*)c.sig + (int64_t)slot * c.k;
+        T* vt = (T*)c.vt + (int64_t)slot * c.k * c.n;
+        for (int e = tid; e < c.k; e += nt) {
+            const T s = zsqrt((T)fmax((double)theta[e], 0.0));
+            sig[e] = (e < kcap && s > rank_tol<T>() * s0) ? s : T(0);
+        }
+        for (int e = tid; e < c.k * c.n; e += nt) {
+            const int cc = e / c.n, i = e - (e / c.n) * c.n;
+            const T s = zsqrt((T)fmax((double)theta[cc], 0.0));
+            const bool live = (cc < kcap && s > rank_tol<T>() * s0);
+            vt[e] = live ? (T)sgn[cc] * V[i * ldv + cc] : T(0);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Tin, typename T>
+__global__ void __launch_bounds__(256) k_form_u(CompressChunk c) {
+    extern __shared__ __align__(16) char dsm[];
+    const int n = c.n, k = c.k, ldn = n + 1;
+    T* Vs = (T*)dsm;                         // k x (n+1)
+    T* As = Vs + (size_t)k * ldn;            // 32 x (n+1)
+    T* sg = As + (size_t)32 * ldn;           // k
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int j = blockIdx.y; j < c.nblk; j += gridDim.y) {
+        const int64_t r0 = (int64_t)j * c.b;
+        const int rows = (int)min((int64_t)c.b, c.rows_total - r0);
+        const int slot = c.slot0 + j;
+        const T* vt = (const T*)c.vt + (int64_t)slot * k * n;
+        const T* sig = (const T*)c.sig + (int64_t)slot * k;
+        T* U = (T*)c.U + (int64_t)slot * c.b * k;
+        const Tin* A = (const Tin*)c.A + r0 * c.lda;
+        for (int e = tid; e < k * n; e += nt) Vs[(e / n) * ldn + (e % n)] = vt[e];
+        for (int e = tid; e < k; e += nt) sg[e] = sig[e];
+        __syncthreads();
+        for (int t0 = blockIdx.x * 32; t0 < c.b; t0 += gridDim.x * 32) {
+            for (int e = tid; e < 32 * n; e += nt) {
+                const int r = e / n, l = e - (e / n) * n;
+                As[r * ldn + l] = (t0 + r < rows) ? T(ld_in(A + (int64_t)(t0 + r) * c.lda + l)) : T(0);
+            }
+            __syncthreads();
+            for (int e = tid; e < 32 * k; e += nt) {
+                const int r = e / k, cc = e - (e / k) * k;
+                if (t0 + r >= c.b) continue;
+                T acc = 0;
+                const T* ar = As + r * ldn;
+                const T* vr = Vs + cc * ldn;
+                for (int l = 0; l < n; ++l) acc += ar[l] * vr[l];
+                const T s = sg[cc];
+                U[(int64_t)(t0 + r) * k + cc] = (t0 + r < rows && s > T(0)) ? acc / s : T(0);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Query phase.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_query(const int64_t* prefix, int nq, int64_t s) {
+    int lo = 0, hi = nq - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct BlockRange { int blk, lo, hi, rows_i; };
+
+// Rows [lo, hi) of block S + t that slab t of query P covers.
+__device__ __forceinline__ BlockRange slab_rows(const QPlan& P, int t, int b, int64_t Trows) {
+    BlockRange r;
+    r.blk = P.S + t;
+    const int64_t row0 = (int64_t)r.blk * b;
+    r.rows_i = (int)min((int64_t)b, Trows - row0);
+    r.lo = (t == 0) ? (int)(P.ts - row0) : 0;
+    r.hi = (t == P.nslab - 1) ? (int)(P.te - row0 + 1) : r.rows_i;
+    return r;
+}
+
+// Partial-SVD (Algorithm 3) of boundary slab `side` of each query:
+//   H = Sigma (X U)^T (X U) Sigma  ->  V~, Sigma~^2   (SVD of X U Sigma, Eq. 5)
+//   slab rows  Sigma~ V~^T V^T   (= Sigma' V'^T, Eq. 6) into M
+//   lift coefficient  Sigma V~ Sigma~^{-1}  (U' = X U Sigma V~ Sigma~^{-1})
+template <typename T, bool REF>
+__global__ void __launch_bounds__(256) k_partial(QueryArgs a) {
+    using TR = typename Prec<T, REF>::TR;
+    extern __shared__ __align__(16) char dsm[];
+    __shared__ JacobiScratch<T> js;
+    __shared__ JacobiScratch<double> jd;
+    __shared__ EigStatic es;
+    __shared__ T sgs[ZS_MAXM];
+    __shared__ T st[ZS_MAXM];
+    const int k = a.k, n = a.n, ld = k + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    SmallEig<T, REF> se;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = dsm + off; off += (bytes + 15) & ~size_t(15); return p; };
+    se.ld = ld;
+    se.A_T = (T*)take(sizeof(T) * k * ld);
+    se.Z_T = (T*)take(sizeof(T) * k * ld);
+    if (REF) {
+        se.A_R = (double*)take(sizeof(double) * k * ld);
+        se.X = (double*)take(sizeof(double) * k * ld);
+        se.W = (double*)take(sizeof(double) * k * ld);
+    }
+    T* Us = (T*)take(sizeof(T) * 64 * ld);   // 64 staged rows of U
+    const int nq = a.hdr->nq;
+    const int64_t Trows = a.hdr->T;
+    const int npair_max = (ZS_MAXM * (ZS_MAXM + 1) / 2 + 255) / 256;
+    for (int p = blockIdx.x; p < 2 * nq; p += gridDim.x) {
+        const int q = p >> 1, side = p & 1;
+        const QPlan& P = a.plans[q];
+        if (side == 1 && P.nslab == 1) continue;
+        const int t = side ? P.nslab - 1 : 0;
+        const BlockRange br = slab_rows(P, t, a.b, Trows);
+        const int ki = min(k, min(br.rows_i, n));
+        const T* U = (const T*)a.U + (int64_t)br.blk * a.b * k;
+        const T* sg = (const T*)a.sig + (int64_t)br.blk * k;
+        const T* vt = (const T*)a.vt + (int64_t)br.blk * k * n;
+        for (int e = tid; e < k; e += nt) sgs[e] = sg[e];
+        // H (upper triangle pairs over ki), FP64-accumulated when REF
+        const int np = ki * (ki + 1) / 2;
+        TR acc[npair_max];
+        int pa[npair_max], pc[npair_max];
+#pragma unroll
+        for (int s = 0; s < npair_max; ++s) {
+            acc[s] = 0;
+            int e = tid + s * nt, aa = 0;
+            while (e >= ki - aa && aa < ki) { e -= ki - aa; ++aa; }
+            pa[s] = aa;
+            pc[s] = aa + e;
+        }
+        for (int r0 = br.lo; r0 < br.hi; r0 += 64) {
+            const int nr = min(64, br.hi - r0);
+            __syncthreads();
+            for (int e = tid; e < nr * k; e += nt) {
+                const int r = e / k, c = e - (e / k) * k;
+                Us[r * ld + c] = U[(int64_t)(r0 + r) * k + c];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < npair_max; ++s) {
+                if (tid + s * nt < np) {
+                    TR sacc = 0;
+                    for (int r = 0; r < nr; ++r) sacc += (TR)Us[r * ld + pa[s]] * (TR)Us[r * ld + pc[s]];
+                    acc[s] += sacc;
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < k * ld; e += nt) se.A_T[e] = T(0);
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < npair_max; ++s) {
+            if (tid + s * nt < np) {
+                const TR h = acc[s] * (TR)sgs[pa[s]] * (TR)sgs[pc[s]];
+                se.A_T[pa[s] * ld + pc[s]] = (T)h;
+                se.A_T[pc[s] * ld + pa[s]] = (T)h;
+                if (REF) {
+                    se.A_R[pa[s] * ld + pc[s]] = (double)h;
+                    se.A_R[pc[s] * ld + pa[s]] = (double)h;
+                }
+            }
+        }
+        __syncthreads();
+        TR* Zo;
+        TR* theta = reinterpret_cast<TR*>(es.theta);
+        small_eig<T, REF>(se, ki, js, jd, theta, es.perm, Zo);
+        // keep r = min(rows, ki) pairs (the rank of X U Sigma)
+        const int r = min(br.hi - br.lo, ki);
+        for (int j = tid; j < k; j += nt) {
+            const T s = (j < r) ? zsqrt((T)fmax((double)theta[j], 0.0)) : T(0);
+            st[j] = s;
+        }
+        __syncthreads();
+        const T s0 = st[0];
+        for (int j = tid; j < k; j += nt)
+            if (!(st[j] > rank_tol<T>() * s0)) st[j] = T(0);
+        __syncthreads();
+        // slab rows of M
+        T* Ms = (T*)a.M + (P.slab0 + t) * k * n;
+        for (int e = tid; e < k * n; e += nt) {
+            const int j = e / n, l = e - (e / n) * n;
+            T v = T(0);
+            if (st[j] > T(0)) {
+                TR accv = 0;
+                const int pj = es.perm[j];
+                for (int aa = 0; aa < ki; ++aa) accv += Zo[aa * ld + pj] * (TR)vt[(int64_t)aa * n + l];
+                v = st[j] * (T)accv;
+            }
+            Ms[e] = v;
+        }
+        // lift coefficients Sigma V~ Sigma~^{-1}  (k x k)
+        T* tc = (T*)a.tco + (int64_t)p * k * k;
+        for (int e = tid; e < k * k; e += nt) {
+            const int aa = e / k, j = e - (e / k) * k;
+            T v = T(0);
+            if (aa < ki && st[j] > T(0)) v = (T)((TR)sgs[aa] * Zo[aa * ld + es.perm[j]] / (TR)st[j]);
+            tc[e] = v;
+        }
+        __syncthreads();
+    }
+}
+
+// Stacked Sigma_i V_i^T of the interior blocks (Algorithm 2, stack step).
+template <typename T>
+__global__ void __launch_bounds__(256) k_stack(QueryArgs a) {
+    const int nq = a.hdr->nq;
+    const int64_t total = a.hdr->nslab_total;
+    const int k = a.k, n = a.n;
+    for (int64_t s = blockIdx.x; s < total; s += gridDim.x) {
+        const int q = find_query(a.slab_prefix, nq, s);
+        const QPlan& P = a.plans[q];
+        const int t = (int)(s - P.slab0);
+        if (t == 0 || t == P.nslab - 1) continue;
+        const int blk = P.S + t;
+        const T* sg = (const T*)a.sig + (int64_t)blk * k;
+        const T* vt = (const T*)a.vt + (int64_t)blk * k * n;
+        T* Ms = (T*)a.M + s * k * n;
+        for (int e = threadIdx.x; e < k * n; e += blockDim.x) Ms[e] = sg[e / n] * vt[e];
+    }
+}
+
+// Stitched core: top-k_q eigenpairs of M^T M -> Sigma_r, V_r; results S, V.
+template <typename T, bool REF, int MB>
+__global__ void __launch_bounds__(256) k_eig_query(QueryArgs a, int m) {
+    extern __shared__ __align__(16) char dsm[];
+    __shared__ JacobiScratch<T> js;
+    __shared__ JacobiScratch<double> jd;
+    __shared__ EigStatic es;
+    __shared__ int sgn[ZS_MAXM];
+    __shared__ int s_rank;
+    EigWork<T, REF> w;
+    eig_carve<T, REF>(dsm, a.n, m, w);
+    const int tid = threadIdx.x, nt = blockDim.x, n = a.n, kq = a.kq, kout = a.kout;
+    const int nq = a.hdr->nq;
+    using TR = typename Prec<T, REF>::TR;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const QPlan& P = a.plans[q];
+        T* V;
+        int ldv;
+        eig_solve<T, REF, MB>((const T*)a.G + (int64_t)q * n * n, n, m, kq, w, js, jd, es, V, ldv);
+        canon_signs<T>(V, ldv, n, kq, sgn);
+        const TR* theta = reinterpret_cast<const TR*>(es.theta);
+        const T s0 = zsqrt((T)fmax((double)theta[0], 0.0));
+        T* sr = (T*)a.sr + (int64_t)q * kq;
+        T* vr = (T*)a.vr + (int64_t)q * kq * n;
+        if (tid == 0) s_rank = 0;
+        __syncthreads();
+        for (int c = tid; c < kout; c += nt) {
+            T s = T(0);
+            if (c < kq) {
+                s = zsqrt((T)fmax((double)theta[c], 0.0));
+                if (!(c < P.kcap && s > rank_tol<T>() * s0)) s = T(0);
+                sr[c] = s;
+            }
+            ((T*)P.S_out)[c] = s;
+            if (s > T(0)) atomicAdd(&s_rank, 1);
+        }
+        __syncthreads();
+        for (int e = tid; e < n * kout; e += nt) {
+            const int i = e / kout, c = e - (e / kout) * kout;
+            T v = T(0);
+            if (c < kq) {
+                const T s = sr[c];
+                v = (s > T(0)) ? (T)sgn[c] * V[i * ldv + c] : T(0);
+                vr[(int64_t)c * n + i] = v;
+            }
+            ((T*)P.V_out)[(int64_t)i * P.ldv + c] = v;
+        }
+        if (tid == 0 && P.rank) *P.rank = s_rank;
+        __syncthreads();
+    }
+}
+
+// U_r = M V_r Sigma_r^{-1} per slab; boundary slabs are pre-multiplied by their
+// Partial-SVD coefficient so that the lift is U_i(rows) C for every slab.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ur(QueryArgs a) {
+    extern __shared__ __align__(16) char dsm[];
+    const int k = a.k, n = a.n, kq = a.kq, ldn = n + 1;
+    T* Vr = (T*)dsm;                          // kq x (n+1)
+    T* Ms = Vr + (size_t)kq * ldn;            // k x (n+1)
+    T* Us = Ms + (size_t)k * ldn;             // k x kq
+    T* Tc = Us + (size_t)k * kq;              // k x k
+    __shared__ T srs[ZS_MAXM];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nq = a.hdr->nq;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const QPlan& P = a.plans[q];
+        const T* vr = (const T*)a.vr + (int64_t)q * kq * n;
+        for (int e = tid; e < kq * n; e += nt) Vr[(e / n) * ldn + (e % n)] = vr[e];
+        for (int e = tid; e < kq; e += nt) srs[e] = ((const T*)a.sr)[(int64_t)q * kq + e];
+        __syncthreads();
+        for (int t = 0; t < P.nslab; ++t) {
+            const int64_t s = P.slab0 + t;
+            const T* Mg = (const T*)a.M + s * k * n;
+            for (int e = tid; e < k * n; e += nt) Ms[(e / n) * ldn + (e % n)] = Mg[e];
+            const bool bnd = (t == 0) || (t == P.nslab - 1);
+            if (bnd) {
+                const int p = 2 * q + ((t == 0) ? 0 : 1);
+                const T* tg = (const T*)a.tco + (int64_t)p * k * k;
+                for (int e = tid; e < k * k; e += nt) Tc[e] = tg[e];
+            }
+            __syncthreads();
+            for (int e = tid; e < k * kq; e += nt) {
+                const int j = e / kq, c = e - (e / kq) * kq;
+                T acc = 0;
+                const T* mr = Ms + j * ldn;
+                const T* vc = Vr + c * ldn;
+                for (int l = 0; l < n; ++l) acc += mr[l] * vc[l];
+                Us[e] = (srs[c] > T(0)) ? acc / srs[c] : T(0);
+            }
+            __syncthreads();
+            T* Cg = (T*)a.C + s * k * kq;
+            if (bnd) {
+                for (int e = tid; e < k * kq; e += nt) {
+                    const int aa = e / kq, c = e - (e / kq) * kq;
+                    T acc = 0;
+                    for (int j = 0; j < k; ++j) acc += Tc[aa * k + j] * Us[j * kq + c];
+                    Cg[e] = acc;
+                }
+            } else {
+                for (int e = tid; e < k * kq; e += nt) Cg[e] = Us[e];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Lift (Eq. 9): output rows of each slab = U_i(rows) C_slab, zero past k_q.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lift(QueryArgs a, int rows_tile) {
+    extern __shared__ __align__(16) char dsm[];
+    const int k = a.k, kq = a.kq, kout = a.kout, ldk = k + 1;
+    T* Cs = (T*)dsm;                          // k x kq
+    T* Ut = Cs + (size_t)k * kq;              // rows_tile x (k+1)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nq = a.hdr->nq;
+    const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
+    for (int64_t s = blockIdx.x; s < total; s += gridDim.x) {
+        const int q = find_query(a.slab_prefix, nq, s);
+        const QPlan& P = a.plans[q];
+        const int t = (int)(s - P.slab0);
+        const BlockRange br = slab_rows(P, t, a.b, Trows);
+        const T* U = (const T*)a.U + (int64_t)br.blk * a.b * k;
+        const T* Cg = (const T*)a.C + s * k * kq;
+        T* out = (T*)P.U;
+        const int64_t o0 = (int64_t)br.blk * a.b + br.lo - P.ts;
+        __syncthreads();
+        for (int e = tid; e < k * kq; e += nt) Cs[e] = Cg[e];
+        for (int r0 = br.lo; r0 < br.hi; r0 += rows_tile) {
+            const int nr = min(rows_tile, br.hi - r0);
+            __syncthreads();
+            for (int e = tid; e < nr * k; e += nt) {
+                const int r = e / k, c = e - (e / k) * k;
+                Ut[r * ldk + c] = U[(int64_t)(r0 + r) * k + c];
+            }
+            __syncthreads();
+            for (int e = tid; e < nr * kout; e += nt) {
+                const int r = e / kout, c = e - (e / kout) * kout;
+                T acc = 0;
+                if (c < kq) {
+                    const T* ur = Ut + r * ldk;
+                    for (int aa = 0; aa < k; ++aa) acc += ur[aa] * Cs[aa * kq + c];
+                }
+                out[(o0 + (r0 - br.lo) + r) * P.ldu + c] = acc;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+int eig_subspace_width(int n, int kq, int extra, bool fp64, bool refine) {
+    if (n <= 64) return n;
+    const bool ref = refine && !fp64;
+    int m = std::min(n, kq + extra);
+    while (m > kq + 2 && eig_smem_bytes(n, m, fp64, ref) > 200 * 1024) --m;
+    if (m > ZS_MAXM) m = ZS_MAXM;
+    if (eig_smem_bytes(n, m, fp64, ref) > 220 * 1024 || m < kq) return -1;
+    return m;
+}
+
+size_t eig_smem_bytes(int n, int m, bool fp64, bool refine) {
+    const size_t ts = fp64 ? 8 : 4;
+    const bool dense = (m == n && n <= 64);
+    const size_t ld = m + 1;
+    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    size_t s = 0;
+    if (!dense) s += 2 * r16(ts * n * ld);
+    s += 2 * r16(ts * m * ld);
+    if (refine && !fp64) s += 3 * r16(8 * m * ld);
+    return s;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define ZS_TRY(x)                                  \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return e_;          \
+    } while (0)
+
+template <typename Tin, typename T, bool REF>
+static cudaError_t compress_impl(const CompressChunk& c, const Tuning& tu, int num_sms, cudaStream_t st) {
+    const int ntile = (c.n + 63) / 64;
+    const int npairs = ntile * (ntile + 1) / 2;
+    dim3 gg(npairs, std::min(c.nblk, 65535));
+    k_gram_compress<Tin, T><<<gg, 256, 0, st>>>(c);
+    ZS_TRY(cudaGetLastError());
+    const bool fp64 = std::is_same<T, double>::value;
+    const int m = eig_subspace_width(c.n, c.k, tu.eig_m_extra, fp64, REF);
+    if (m < 0) return cudaErrorInvalidValue;
+    const size_t sm = eig_smem_bytes(c.n, m, fp64, REF);
+    const int grid_e = std::min(c.nblk, 65535);
+    if (m <= 32) {
+        ZS_TRY(set_smem(k_eig_compress<T, REF, 32>, sm));
+        k_eig_compress<T, REF, 32><<<grid_e, 256, sm, st>>>(c, m);
+    } else {
+        ZS_TRY(set_smem(k_eig_compress<T, REF, 64>, sm));
+        k_eig_compress<T, REF, 64><<<grid_e, 256, sm, st>>>(c, m);
+    }
+    ZS_TRY(cudaGetLastError());
+    const size_t smu = sizeof(T) * ((size_t)c.k * (c.n + 1) + 32 * (size_t)(c.n + 1) + c.k) + 64;
+    ZS_TRY(set_smem(k_form_u<Tin, T>, smu));
+    dim3 gu(std::min((c.b + 31) / 32, 8), std::min(c.nblk, 65535));
+    k_form_u<Tin, T><<<gu, 256, smu, st>>>(c);
+    ZS_TRY(cudaGetLastError());
+    note_launches(3);
+    (void)num_sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
+                            cudaStream_t st) {
+    const bool ref = (flags & 1) != 0;
+    if (fp64) return compress_impl<double, double, false>(c, tu, num_sms, st);
+    if (c.in_kind == IN_BF16)
+        return ref ? compress_impl<__nv_bfloat16, float, true>(c, tu, num_sms, st)
+                   : compress_impl<__nv_bfloat16, float, false>(c, tu, num_sms, st);
+    return ref ? compress_impl<float, float, true>(c, tu, num_sms, st)
+               : compress_impl<float, float, false>(c, tu, num_sms, st);
+}
+
+template <typename T, bool REF>
+static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs, const Tuning& tu,
+                              int num_sms, cudaStream_t st) {
+    const bool fp64 = std::is_same<T, double>::value;
+    const int k = a.k, n = a.n, kq = a.kq;
+    const int pers = std::max(1, num_sms * tu.slab_ctas_per_sm);
+    // Partial-SVD
+    {
+        const int ld = k + 1;
+        auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+        size_t sm = 2 * r16(sizeof(T) * k * ld) + r16(sizeof(T) * 64 * ld);
+        if (REF) sm += 3 * r16(sizeof(double) * k * ld);
+        ZS_TRY(set_smem(k_partial<T, REF>, sm));
+        k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
+    ZS_TRY(cudaGetLastError());
+    {
+        const int ntile = (n + 63) / 64;
+        const int npairs = ntile * (ntile + 1) / 2;
+        dim3 gg(npairs, std::min(max_nq, 65535));
+        k_gram_query<T><<<gg, 256, 0, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        const int m = eig_subspace_width(n, kq, tu.eig_m_extra, fp64, REF);
+        if (m < 0) return cudaErrorInvalidValue;
+        const size_t sm = eig_smem_bytes(n, m, fp64, REF);
+        const int grid = std::min(max_nq, 65535);
+        if (m <= 32) {
+            ZS_TRY(set_smem(k_eig_query<T, REF, 32>, sm));
+            k_eig_query<T, REF, 32><<<grid, 256, sm, st>>>(a, m);
+        } else {
+            ZS_TRY(set_smem(k_eig_query<T, REF, 64>, sm));
+            k_eig_query<T, REF, 64><<<grid, 256, sm, st>>>(a, m);
+        }
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        const size_t sm = sizeof(T) * ((size_t)kq * (n + 1) + (size_t)k * (n + 1) + (size_t)k * kq + (size_t)k * k) + 64;
+        ZS_TRY(set_smem(k_ur<T>, sm));
+        k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        const int rt = tu.lift_rows;
+        const size_t sm = sizeof(T) * ((size_t)k * kq + (size_t)rt * (k + 1)) + 64;
+        ZS_TRY(set_smem(k_lift<T>, sm));
+        k_lift<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, sm, st>>>(a, rt);
+        ZS_TRY(cudaGetLastError());
+    }
+    note_launches(6);
+    return cudaSuccess;
+}
+
+cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, const Tuning& tu,
+                         int num_sms, cudaStream_t st) {
+    if (fp64) return query_impl<double, false>(a, max_nq, max_slabs, tu, num_sms, st);
+    return a.fp64_refine ? query_impl<float, true>(a, max_nq, max_slabs, tu, num_sms, st)
+                         : query_impl<float, false>(a, max_nq, max_slabs, tu, num_sms, st);
+}
+
+}  // namespace zs

@@ -1,0 +1,222 @@
+// zs_linalg.cuh - CTA-wide dense linear algebra used by the range-SVD kernels.
+//
+// Every routine here is called by all threads of one CTA with the operands in
+// shared memory (or, for the n x n Gram matrix, in L2-resident global memory)
+// and contains its own __syncthreads().  Nothing spins: every loop has a fixed
+// upper bound.
+//
+//  * jacobi_eig   cyclic two-sided Jacobi eigensolver for a symmetric m x m
+//                 matrix (m <= ZS_MAXM), round-robin ("circle") ordering so the
+//                 m/2 rotations of one step are disjoint and applied in
+//                 parallel.  Two-sided Jacobi on X^T X performs the rotations
+//                 of one-sided (Hestenes) Jacobi on X, so this is the
+//                 "small-core Jacobi SVD" of every Gram-form core below.
+//  * mgs_orth     modified Gram-Schmidt (two passes) of an n x m column block
+//                 with replacement of numerically dependent columns.
+//  * sort_desc    permutation that orders eigenvalues descending.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#ifndef ZS_MAXM
+#define ZS_MAXM 64
+#endif
+
+namespace zs {
+
+template <typename T> __device__ __forceinline__ T eps_of();
+template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+
+__device__ __forceinline__ float zsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double zsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float zabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double zabs(double x) { return fabs(x); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// CTA-wide sum; `red` is shared scratch of >= 32 elements.  Result returned to
+// every thread.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T r = 0;
+    for (int i = 0; i < nw; ++i) r += red[i];
+    return r;
+}
+
+// Pair (p, q), p < q, of slot i in step r of the round-robin schedule over mm
+// (even) indices: index 0 stays, the others rotate.  Over mm - 1 steps every
+// pair meets exactly once.
+__device__ __forceinline__ void rr_pair(int mm, int r, int i, int& p, int& q) {
+    const int a = (i == 0) ? 0 : ((i - 1 + r) % (mm - 1)) + 1;
+    const int b = ((mm - 2 - i + r) % (mm - 1)) + 1;
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+}
+
+// Shared scratch the Jacobi routine needs (static size).
+template <typename T>
+struct JacobiScratch {
+    T cs[ZS_MAXM];        // c, s per pair
+    int pq[ZS_MAXM];      // p, q per pair
+    int flag;
+    T scale;
+};
+
+// Symmetric eigen-decomposition A = Z diag(lambda) Z^T, in place: on return the
+// diagonal of A holds the eigenvalues (unsorted) and the columns of Z the
+// eigenvectors.  If init_z, Z starts as the identity, else the rotations are
+// accumulated into the Z given (warm start / refinement).  Returns sweeps used.
+template <typename T>
+__device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>& js,
+                          int max_sweeps, bool init_z) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (init_z)
+        for (int e = tid; e < m * m; e += nt) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
+    if (tid == 0) {
+        T mx = 0;
+        for (int i = 0; i < m; ++i) mx = fmax(mx, zabs(A[i * lda + i]));
+        js.scale = mx;
+    }
+    __syncthreads();
+    if (m < 2) return 0;
+    const int mm = m + (m & 1), np = mm >> 1;
+    const T tol = T(2) * eps_of<T>();
+    const T floor_ = eps_of<T>() * js.scale;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) js.flag = 0;
+        __syncthreads();
+        for (int r = 0; r < mm - 1; ++r) {
+            for (int i = tid; i < np; i += nt) {
+                int p, q;
+                rr_pair(mm, r, i, p, q);
+                T c = 1, s = 0;
+                if (q < m) {
+                    const T apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
+                    const T aa = zabs(apq);
+                    if (aa > floor_ && aa > tol * zsqrt(zabs(app * aqq))) {
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (zabs(tau) + zsqrt(T(1) + tau * tau));
+                        c = T(1) / zsqrt(T(1) + t * t);
+                        s = t * c;
+                        js.flag = 1;
+                    }
+                }
+                js.pq[2 * i] = p;
+                js.pq[2 * i + 1] = q;
+                js.cs[2 * i] = c;
+                js.cs[2 * i + 1] = s;
+            }
+            __syncthreads();
+            // rows:  A <- J^T A
+            for (int e = tid; e < np * m; e += nt) {
+                const int i = e / m, j = e - (e / m) * m;
+                const T s = js.cs[2 * i + 1];
+                if (s == T(0)) continue;
+                const T c = js.cs[2 * i];
+                const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
+                const T ap = A[p * lda + j], aq = A[q * lda + j];
+                A[p * lda + j] = c * ap - s * aq;
+                A[q * lda + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J,  Z <- Z J
+            for (int e = tid; e < np * m; e += nt) {
+                const int i = e / m, row = e - (e / m) * m;
+                const T s = js.cs[2 * i + 1];
+                if (s == T(0)) continue;
+                const T c = js.cs[2 * i];
+                const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
+                const T ap = A[row * lda + p], aq = A[row * lda + q];
+                A[row * lda + p] = c * ap - s * aq;
+                A[row * lda + q] = s * ap + c * aq;
+                const T zp = Z[row * ldz + p], zq = Z[row * ldz + q];
+                Z[row * ldz + p] = c * zp - s * zq;
+                Z[row * ldz + q] = s * zp + c * zq;
+            }
+            __syncthreads();
+        }
+        const int f = js.flag;
+        __syncthreads();
+        if (!f) break;
+    }
+    return sweep;
+}
+
+// perm[r] = index of the r-th largest diagonal entry of A (stable on ties).
+template <typename T>
+__device__ void sort_desc(const T* A, int lda, int m, int* perm) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const T v = A[i * lda + i];
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const T w = A[j * lda + j];
+            rk += (w > v) || (w == v && j < i);
+        }
+        perm[rk] = i;
+    }
+    __syncthreads();
+}
+
+// Orthonormalise the m columns of Q (n x m, row stride ldq, best odd) in
+// place by classical Gram-Schmidt with a second projection pass (CGS2).  A
+// column whose norm collapses below 1e3*eps of its starting norm (rank
+// deficiency) is replaced by a coordinate vector and re-projected.  `red` is
+// shared scratch (>= 32), `coef` shared scratch (>= m).
+template <typename T>
+__device__ void mgs_orth(T* Q, int ldq, int n, int m, T* red, T* coef) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, wid = tid >> 5, nw = (nt + 31) >> 5;
+    for (int c = 0; c < m; ++c) {
+        T ss = 0;
+        for (int i = tid; i < n; i += nt) ss += Q[i * ldq + c] * Q[i * ldq + c];
+        const T nrm0 = zsqrt(block_sum(ss, red));
+        T nrm = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (attempt == 1) {
+                __syncthreads();
+                for (int i = tid; i < n; i += nt) Q[i * ldq + c] = T(0);
+                __syncthreads();
+                if (tid == 0) Q[((c * 7919 + 13) % n) * ldq + c] = T(1);
+                __syncthreads();
+            }
+            for (int pass = 0; pass < 2 && c > 0; ++pass) {
+                for (int d = wid; d < c; d += nw) {
+                    T dot = 0;
+                    for (int i = lane; i < n; i += 32) dot += Q[i * ldq + d] * Q[i * ldq + c];
+                    dot = warp_sum(dot);
+                    if (lane == 0) coef[d] = dot;
+                }
+                __syncthreads();
+                for (int i = tid; i < n; i += nt) {
+                    T acc = Q[i * ldq + c];
+                    for (int d = 0; d < c; ++d) acc -= coef[d] * Q[i * ldq + d];
+                    Q[i * ldq + c] = acc;
+                }
+                __syncthreads();
+            }
+            ss = 0;
+            for (int i = tid; i < n; i += nt) ss += Q[i * ldq + c] * Q[i * ldq + c];
+            nrm = zsqrt(block_sum(ss, red));
+            const T base = attempt == 0 ? nrm0 : T(1);
+            if (nrm > T(1e3) * eps_of<T>() * base && nrm > T(0)) break;
+        }
+        const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+        for (int i = tid; i < n; i += nt) Q[i * ldq + c] *= inv;
+        __syncthreads();
+    }
+}
+
+}  // namespace zs

@@ -1,0 +1,254 @@
+"""Thin ctypes binding over ``libzoomsvd.so`` (the C ABI in include/zoomsvd.h).
+
+Argument marshalling only: every step of the range-SVD path runs in the
+library's CUDA kernels.  PyTorch supplies device memory for results and the
+current CUDA stream.  If the library is missing, importing this module raises
+— there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libzoomsvd.so")
+
+ZS_F64, ZS_F32, ZS_BF16 = 0, 1, 2
+ZS_FLAG_FP64_REFINE = 1
+DTYPES = {"f64": ZS_F64, "f32": ZS_F32, "bf16": ZS_BF16}
+STATUS = {0: "ZS_OK", 1: "ZS_EINVAL", 2: "ZS_ERANGE", 3: "ZS_ENOMEM", 4: "ZS_EBUSY",
+          5: "ZS_ETIMEDOUT", 6: "ZS_EDTYPE", 7: "ZS_ECUDA", 8: "ZS_EINTERNAL", 9: "ZS_ENOTFOUND"}
+
+
+class ZsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class StoreConfig(C.Structure):
+    _fields_ = [("n", C.c_int64), ("b", C.c_int64), ("k", C.c_int32), ("in_dtype", C.c_int32),
+                ("capacity_rows", C.c_int64), ("device", C.c_int32), ("flags", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("U", C.c_void_p), ("ldu", C.c_int64), ("S", C.c_void_p), ("V", C.c_void_p),
+                ("ldv", C.c_int64), ("rank", C.c_void_p)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("max_inflight", C.c_int32), ("queue_capacity", C.c_int32),
+                ("memory_budget", C.c_int64)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("rejected", C.c_int64), ("batches", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("mean_ms", C.c_double), ("wall_s", C.c_double), ("queries_per_s", C.c_double),
+                ("mean_batch", C.c_double)]
+
+
+# name -> (restype, argtypes); exactly the functions include/zoomsvd.h declares
+SIGNATURES = {
+    "zs_store_create": (C.c_int, [C.POINTER(StoreConfig), C.POINTER(C.c_void_p)]),
+    "zs_store_destroy": (None, [C.c_void_p]),
+    "zs_store_append": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
+    "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "zs_store_export_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "zs_query": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(Result), C.c_void_p]),
+    "zs_query_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32, C.c_int32,
+                                 C.POINTER(Result), C.c_void_p]),
+    "zs_serve_start": (C.c_int, [C.c_void_p, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
+    "zs_serve_submit": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(Result),
+                                  C.POINTER(C.c_uint64)]),
+    "zs_serve_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "zs_serve_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int64, C.POINTER(C.c_int32)]),
+    "zs_serve_stop": (C.c_int, [C.c_void_p, C.POINTER(ServeStats)]),
+    "zs_status_str": (C.c_char_p, [C.c_int]),
+    "zs_last_error": (C.c_char_p, []),
+    "zs_launch_count": (C.c_int64, []),
+}
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libzoomsvd.so not built ({path}); run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise ZsError(status, lib().zs_last_error().decode())
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def factor_dtype(dtype: str) -> torch.dtype:
+    return torch.float64 if dtype == "f64" else torch.float32
+
+
+class QueryOut:
+    """Device tensors of one range-SVD result."""
+
+    def __init__(self, rows: int, n: int, k_out: int, dtype: torch.dtype, device):
+        self.U = torch.empty((rows, k_out), dtype=dtype, device=device)
+        self.S = torch.empty((k_out,), dtype=dtype, device=device)
+        self.V = torch.empty((n, k_out), dtype=dtype, device=device)
+        self.rank = torch.zeros((1,), dtype=torch.int32, device=device)
+
+    def as_c(self) -> Result:
+        return Result(self.U.data_ptr(), self.U.stride(0), self.S.data_ptr(), self.V.data_ptr(),
+                      self.V.stride(0), self.rank.data_ptr())
+
+
+class Store:
+    """A compressed range-SVD store on one GPU (the sets U, S, V of Def. 2)."""
+
+    def __init__(self, n: int, b: int, k: int, dtype: str = "f32", capacity_rows: int = 1 << 20,
+                 device: int = 0, fp64_refine: bool = False):
+        self.n, self.b, self.k, self.dtype = n, b, k, dtype
+        self.device = torch.device("cuda", device)
+        self.fdtype = factor_dtype(dtype)
+        cfg = StoreConfig(n, b, k, DTYPES[dtype], capacity_rows, device,
+                          ZS_FLAG_FP64_REFINE if fp64_refine else 0)
+        h = C.c_void_p()
+        _check(lib().zs_store_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().zs_store_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def append(self, rows, stream=None):
+        """Append rows (torch CUDA tensor, or numpy/CPU tensor copied by the library).
+
+        bf16 rows are given as int16/uint16 bit patterns or torch.bfloat16.
+        """
+        if isinstance(rows, np.ndarray):
+            arr = np.ascontiguousarray(rows)
+            ld = arr.strides[0] // arr.itemsize
+            _check(lib().zs_store_append(self._h, arr.ctypes.data, arr.shape[0], ld, 0, _stream_ptr(stream)))
+            return
+        t = rows
+        if t.dim() != 2 or t.stride(1) != 1:
+            t = t.contiguous()
+        on_dev = 1 if t.is_cuda else 0
+        _check(lib().zs_store_append(self._h, t.data_ptr(), t.shape[0], t.stride(0), on_dev, _stream_ptr(stream)))
+
+    def info(self):
+        T, nb, by = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().zs_store_info(self._h, C.byref(T), C.byref(nb), C.byref(by)))
+        return T.value, nb.value, by.value
+
+    def export_block(self, i: int, stream=None):
+        U = torch.empty((self.b, self.k), dtype=self.fdtype, device=self.device)
+        s = torch.empty((self.k,), dtype=self.fdtype, device=self.device)
+        Vt = torch.empty((self.k, self.n), dtype=self.fdtype, device=self.device)
+        r, kk = C.c_int32(), C.c_int32()
+        _check(lib().zs_store_export_block(self._h, i, U.data_ptr(), s.data_ptr(), Vt.data_ptr(),
+                                           C.byref(r), C.byref(kk), _stream_ptr(stream)))
+        return U[: r.value], s, Vt, kk.value
+
+    def new_result(self, ts: int, te: int, k_out: int) -> QueryOut:
+        return QueryOut(te - ts + 1, self.n, k_out, self.fdtype, self.device)
+
+    def query(self, ts: int, te: int, k_out: int | None = None, out: QueryOut | None = None, stream=None):
+        k_out = self.k if k_out is None else k_out
+        out = out or self.new_result(ts, te, k_out)
+        r = out.as_c()
+        _check(lib().zs_query(self._h, ts, te, k_out, C.byref(r), _stream_ptr(stream)))
+        return out
+
+    def query_batch(self, ts, te, k_out: int | None = None, outs=None, stream=None):
+        k_out = self.k if k_out is None else k_out
+        ts = np.ascontiguousarray(ts, dtype=np.int64)
+        te = np.ascontiguousarray(te, dtype=np.int64)
+        nq = ts.shape[0]
+        if outs is None:
+            outs = [self.new_result(int(a), int(z), k_out) for a, z in zip(ts, te)]
+        res = (Result * nq)(*[o.as_c() for o in outs])
+        _check(lib().zs_query_batch(self._h, ts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    te.ctypes.data_as(C.POINTER(C.c_int64)), nq, k_out, res,
+                                    _stream_ptr(stream)))
+        return outs
+
+
+class Server:
+    """Continuous-batching query server over a Store."""
+
+    def __init__(self, store: Store, max_batch=256, max_inflight=2, queue_capacity=1 << 16,
+                 memory_budget=4 << 30):
+        self.store = store
+        cfg = ServeConfig(max_batch, max_inflight, queue_capacity, memory_budget)
+        h = C.c_void_p()
+        _check(lib().zs_serve_start(store.handle, C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, ts: int, te: int, k_out: int | None = None, out: QueryOut | None = None):
+        k_out = self.store.k if k_out is None else k_out
+        out = out or self.store.new_result(ts, te, k_out)
+        r = out.as_c()
+        t = C.c_uint64()
+        st = lib().zs_serve_submit(self._h, ts, te, k_out, C.byref(r), C.byref(t))
+        if st != 0:
+            raise ZsError(st, lib().zs_last_error().decode())
+        self._keep[t.value] = out
+        return t.value, out
+
+    def poll(self, ticket: int):
+        d, s = C.c_int32(), C.c_int32()
+        _check(lib().zs_serve_poll(self._h, ticket, C.byref(d), C.byref(s)))
+        if d.value:
+            self._keep.pop(ticket, None)
+        return bool(d.value), s.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000):
+        s = C.c_int32()
+        _check(lib().zs_serve_wait(self._h, ticket, timeout_ms, C.byref(s)))
+        self._keep.pop(ticket, None)
+        return s.value
+
+    def stop(self) -> dict:
+        st = ServeStats()
+        _check(lib().zs_serve_stop(self._h, C.byref(st)))
+        self._h = None
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
+
+def launch_count() -> int:
+    return int(lib().zs_launch_count())
