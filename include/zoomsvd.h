@@ -114,6 +114,10 @@ void zs_store_destroy(zs_store* st);
 zs_status zs_store_append(zs_store* st, const void* rows, int64_t nrows, int64_t ld,
                           int32_t rows_on_device, void* stream);
 
+/* Forget every appended row (the factor arrays stay allocated), so the store
+ * can be refilled.  Waits for the store's outstanding work to finish.      */
+zs_status zs_store_reset(zs_store* st);
+
 /* Host-side counters: rows appended, blocks (closed + open), and device
  * bytes held by the compressed factors (Theorem 3).  Any pointer may be
  * NULL.                                                                     */
@@ -203,6 +207,16 @@ const char* zs_last_error(void);
 /* Number of kernel launches the library has issued in this process (all
  * stores), for launch accounting.                                          */
 int64_t zs_launch_count(void);
+
+/* Kernel profiler (tracing).  While enabled, every kernel launch is
+ * bracketed by CUDA events recorded on its launch stream; zs_profile_get
+ * synchronises on those events and reports, for the i-th kernel name seen,
+ * its launch count and summed device time.  zs_profile_reset clears the
+ * table.  Off by default; costs two event records per launch when on.     */
+void zs_profile_enable(int32_t on);
+void zs_profile_reset(void);
+int32_t zs_profile_count(void);
+zs_status zs_profile_get(int32_t i, const char** name, int64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

@@ -68,7 +68,7 @@ void QueryExec::release() {
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     auto fh = [](void*& p) { if (p) cudaFreeHost(p); p = nullptr; };
     if (done) { cudaEventSynchronize(done); cudaEventDestroy(done); done = nullptr; }
-    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C);
+    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C); f(ews);
     fh(h_blob);
     cap_nq = 0;
     cap_slabs = 0;
@@ -101,6 +101,8 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
     if ((s = al(&vr, ts * (size_t)want_nq * want_kq * n, "v")) != ZS_OK) return s;
     if ((s = al(&tco, ts * (size_t)2 * want_nq * k * k, "partial")) != ZS_OK) return s;
     if ((s = al(&C, ts * want_sl * k * want_kq, "lift coeff")) != ZS_OK) return s;
+    ews_ctas = std::max(1, st.num_sms);
+    if ((s = al(&ews, eig_ws_bytes((int)n, st.fp64, ews_ctas), "eigen workspace")) != ZS_OK) return s;
     cap_nq = want_nq;
     cap_slabs = want_sl;
     cap_kq = want_kq;
@@ -197,6 +199,8 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.vr = x.vr;
     a.tco = x.tco;
     a.C = x.C;
+    a.ews = x.ews;
+    a.ews_ctas = x.ews_ctas;
     cudaError_t e = launch_query(a, st.fp64, nq, nslab, st.tune, st.num_sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "query kernels");
     ZS_CU(cudaEventRecord(x.done, stream), "event record");
@@ -229,6 +233,8 @@ static zs_status store_alloc(zs_store* st) {
     const size_t gper = ts * (size_t)c.n * c.n;
     st->gchunk = (int)std::max<size_t>(1, std::min<size_t>(st->gram_budget / gper, 65535));
     if ((s = al(&st->gscr, gper * st->gchunk, "gram scratch")) != ZS_OK) return s;
+    st->ews_ctas = std::max(1, st->num_sms);
+    if ((s = al(&st->ews, eig_ws_bytes((int)c.n, st->fp64, st->ews_ctas), "eigen workspace")) != ZS_OK) return s;
     // host staging: two device buffers of whole blocks
     const size_t blk_bytes = st->insize * (size_t)c.b * c.n;
     st->stage_blocks = (int)std::max<size_t>(1, std::min<size_t>(st->stage_budget / blk_bytes, st->gchunk));
@@ -267,7 +273,7 @@ extern "C" zs_status zs_store_create(const zs_store_config* cfg, zs_store** out)
     }
     const bool fp64 = (c.in_dtype == ZS_F64);
     const bool ref = (c.flags & ZS_FLAG_FP64_REFINE) && !fp64;
-    if (eig_subspace_width((int)c.n, c.k, 16, fp64, ref) < 0)
+    if (!eig_plan((int)c.n, c.k, 16, fp64, ref).ok)
         return fail(ZS_EINVAL, "n=%lld with k=%d does not fit the eigen core's shared memory", (long long)c.n, c.k);
     DeviceGuard g(c.device);
     zs_store* st = new zs_store();
@@ -292,7 +298,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     cudaDeviceSynchronize();
     st->qx.release();
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
-    f(st->U); f(st->sig); f(st->vt); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]);
+    f(st->U); f(st->sig); f(st->vt); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
@@ -326,6 +332,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.U = st->U;
         ch.sig = st->sig;
         ch.vt = st->vt;
+        ch.ews = st->ews;
+        ch.ews_ctas = st->ews_ctas;
         cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, stream);
         if (e != cudaSuccess) return cuda_fail(e, "compression kernels");
     }
@@ -419,6 +427,16 @@ extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nro
     return ZS_OK;
 }
 
+extern "C" zs_status zs_store_reset(zs_store* st) {
+    if (!st) return fail(ZS_EINVAL, "null store");
+    std::lock_guard<std::mutex> lk(st->mu);
+    DeviceGuard g(st->cfg.device);
+    ZS_CU(cudaEventSynchronize(st->append_done), "reset wait");
+    if (st->qx.done) ZS_CU(cudaEventSynchronize(st->qx.done), "reset wait");
+    st->T = 0;
+    return ZS_OK;
+}
+
 extern "C" zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks, int64_t* bytes) {
     if (!st) return fail(ZS_EINVAL, "null store");
     const int64_t T = st->T, b = st->cfg.b;
@@ -457,6 +475,10 @@ namespace zs {
 zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, const int64_t* te, int nq, int kout,
                              const zs_result* res, cudaStream_t stream, int64_t Trows) {
     const int kq = std::min<int>(kout, (int)st->cfg.n);
+    const bool ref = (st->cfg.flags & ZS_FLAG_FP64_REFINE) && !st->fp64;
+    if (!eig_plan((int)st->cfg.n, kq, st->tune.eig_m_extra, st->fp64, ref).ok)
+        return fail(ZS_EINVAL, "k_out=%d with n=%lld does not fit the eigen core's shared memory", kout,
+                    (long long)st->cfg.n);
     std::vector<QPlan> plans;
     std::vector<int64_t> prefix;
     zs_status s = plan_queries(*st, Trows, ts, te, nq, kq, plans, prefix);
@@ -536,3 +558,11 @@ extern "C" const char* zs_status_str(zs_status s) {
 extern "C" const char* zs_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int64_t zs_launch_count(void) { return launch_count_total(); }
+
+extern "C" void zs_profile_enable(int32_t on) { profile_enable(on); }
+extern "C" void zs_profile_reset(void) { profile_reset(); }
+extern "C" int32_t zs_profile_count(void) { return profile_count(); }
+extern "C" zs_status zs_profile_get(int32_t i, const char** name, int64_t* launches, double* total_ms) {
+    if (!profile_get(i, name, launches, total_ms)) return fail(ZS_ENOTFOUND, "no profile entry %d", i);
+    return ZS_OK;
+}

@@ -21,6 +21,8 @@ struct QueryExec {
     void* h_blob = nullptr;       // pinned mirror
     size_t blob_bytes = 0;
     void *M = nullptr, *G = nullptr, *sr = nullptr, *vr = nullptr, *tco = nullptr, *C = nullptr;
+    void* ews = nullptr;
+    int ews_ctas = 1;
     cudaEvent_t done = nullptr;   // last batch that used this scratch
     ~QueryExec();
     void release();
@@ -52,6 +54,8 @@ struct zs_store {
     void* vt = nullptr;            // cap_blocks x k x n
     void* tail = nullptr;          // b x n raw rows of the open block
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
+    void* ews = nullptr;           // eigen-core workspace
+    int ews_ctas = 1;
     int gchunk = 1;
     size_t gram_budget = (size_t)64 << 20;
     void* stage[2] = {nullptr, nullptr};

@@ -32,6 +32,8 @@ struct CompressChunk {
     void* U;          // store: slot-major, b * k per slot
     void* sig;        // store: k per slot
     void* vt;         // store: k * n per slot
+    void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
+    int32_t ews_ctas;
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).
@@ -81,6 +83,8 @@ struct QueryArgs {
     void* vr;         // nq * kq * n             stitched right vectors (transposed)
     void* tco;        // 2 * nq * k * k          Partial-SVD lift coefficients
     void* C;          // nslab_total * k * kq    lift coefficients per slab
+    void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
+    int32_t ews_ctas;
 };
 
 // Launch configuration chosen by the autotuner (or defaults).
@@ -97,8 +101,19 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
                             int num_sms, cudaStream_t st);
 cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs,
                          const Tuning& tu, int num_sms, cudaStream_t st);
-int eig_subspace_width(int n, int kq, int extra, bool fp64, bool refine);
-size_t eig_smem_bytes(int n, int m, bool fp64, bool refine);
+struct EigPlan {
+    int m = 0;          // subspace width (n for the dense path)
+    bool yglob = false; // Y block in global workspace
+    size_t smem = 0;    // dynamic shared memory bytes
+    bool ok = false;
+};
+EigPlan eig_plan(int n, int kq, int extra, bool fp64, bool refine);
+size_t eig_smem_bytes(int n, int m, bool fp64, bool refine, bool yglob);
+size_t eig_ws_bytes(int n, bool fp64, int ctas);
 void note_launches(int64_t n);
+void profile_enable(int on);
+void profile_reset();
+int profile_count();
+bool profile_get(int i, const char** name, int64_t* launches, double* ms);
 
 }  // namespace zs

@@ -16,7 +16,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <string>
 #include <type_traits>
+#include <vector>
 
 #include "zs_internal.h"
 #include "zs_linalg.cuh"
@@ -26,6 +29,81 @@ namespace zs {
 static std::atomic<int64_t> g_launches{0};
 void note_launches(int64_t n) { g_launches += n; }
 int64_t launch_count_total() { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// Kernel profiler: CUDA events around each launch, on the launch stream.
+// ---------------------------------------------------------------------------
+namespace prof {
+struct Pending { int id; cudaEvent_t a, b; };
+struct Entry { std::string name; int64_t launches = 0; double ms = 0; };
+static std::atomic<int> g_on{0};
+static std::mutex g_mu;
+static std::vector<Pending> g_pending;
+static std::vector<Entry> g_table;
+static std::vector<cudaEvent_t> g_pool;
+
+static cudaEvent_t get_event() {
+    if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+static void drain_locked() {
+    for (auto& p : g_pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        g_table[p.id].launches += 1;
+        g_table[p.id].ms += ms;
+        g_pool.push_back(p.a);
+        g_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+struct Scope {
+    int id = -1;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t st;
+    Scope(const char* name, cudaStream_t s) : st(s) {
+        if (!g_on.load(std::memory_order_relaxed)) return;
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (size_t i = 0; i < g_table.size(); ++i)
+            if (g_table[i].name == name) { id = (int)i; break; }
+        if (id < 0) { g_table.push_back(Entry{name}); id = (int)g_table.size() - 1; }
+        a = get_event();
+        b = get_event();
+        cudaEventRecord(a, st);
+    }
+    ~Scope() {
+        if (id < 0) return;
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_pending.push_back(Pending{id, a, b});
+        if (g_pending.size() > 4096) drain_locked();
+    }
+};
+}  // namespace prof
+
+void profile_enable(int on) { prof::g_on.store(on); }
+void profile_reset() {
+    std::lock_guard<std::mutex> lk(prof::g_mu);
+    prof::drain_locked();
+    prof::g_table.clear();
+}
+int profile_count() {
+    std::lock_guard<std::mutex> lk(prof::g_mu);
+    prof::drain_locked();
+    return (int)prof::g_table.size();
+}
+bool profile_get(int i, const char** name, int64_t* launches, double* ms) {
+    std::lock_guard<std::mutex> lk(prof::g_mu);
+    prof::drain_locked();
+    if (i < 0 || i >= (int)prof::g_table.size()) return false;
+    if (name) *name = prof::g_table[i].name.c_str();
+    if (launches) *launches = prof::g_table[i].launches;
+    if (ms) *ms = prof::g_table[i].ms;
+    return true;
+}
 
 __device__ __forceinline__ double ld_in(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld_in(const float* p) { return __ldg(p); }
@@ -187,25 +265,27 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
 // ---------------------------------------------------------------------------
 template <typename T, bool REF>
 struct EigWork {
-    T* Q;       // n x ldq
-    T* Y;       // n x ldq
+    T* Q;       // n x ldq, shared memory
+    T* Y;       // n x ldq, shared memory or (yglob) this CTA's global workspace
     int ldq;
+    bool yglob;
     SmallEig<T, REF> se;
 };
 
 template <typename T, bool REF>
-__device__ __forceinline__ size_t eig_carve(char* base, int n, int m, EigWork<T, REF>& w) {
+__device__ __forceinline__ size_t eig_carve(char* base, int n, int m, bool yglob, void* ws, EigWork<T, REF>& w) {
     size_t off = 0;
     auto take = [&](size_t bytes) { char* p = base + off; off += (bytes + 15) & ~size_t(15); return p; };
     const bool dense = (m == n && n <= 64);
     const int ld = m + 1;
     w.ldq = ld;
+    w.yglob = yglob && !dense;
     if (dense) {
         w.Q = nullptr;
         w.Y = nullptr;
     } else {
         w.Q = (T*)take(sizeof(T) * (size_t)n * ld);
-        w.Y = (T*)take(sizeof(T) * (size_t)n * ld);
+        w.Y = w.yglob ? (T*)ws + (size_t)blockIdx.x * n * ld : (T*)take(sizeof(T) * (size_t)n * ld);
     }
     w.se.ld = ld;
     w.se.A_T = (T*)take(sizeof(T) * (size_t)m * ld);
@@ -366,9 +446,17 @@ __device__ void eig_solve(const T* __restrict__ G, int n, int m, int kw, EigWork
         __syncthreads();
         if (done || it == maxit - 1) break;
         // next block: orthonormalised Ritz-rotated G Q
-        T* t = Q;
-        Q = Y;
-        Y = t;
+        if (w.yglob) {
+            for (int e = tid; e < n * m; e += nt) {
+                const int i = e / m, c = e - (e / m) * m;
+                Q[i * ldq + c] = Y[i * ldq + c];
+            }
+            __syncthreads();
+        } else {
+            T* t = Q;
+            Q = Y;
+            Y = t;
+        }
         mgs_orth<T>(Q, ldq, n, m, red, coef);
     }
     V = Q;
@@ -406,14 +494,14 @@ template <> __device__ __forceinline__ double rank_tol<double>() { return kRankT
 // Storage phase: eigen-core per block, then U = A V Sigma^-1.
 // ---------------------------------------------------------------------------
 template <typename T, bool REF, int MB>
-__global__ void __launch_bounds__(256) k_eig_compress(CompressChunk c, int m) {
+__global__ void __launch_bounds__(256) k_eig_compress(CompressChunk c, int m, int yglob, void* ws) {
     extern __shared__ __align__(16) char dsm[];
     __shared__ JacobiScratch<T> js;
     __shared__ JacobiScratch<double> jd;
     __shared__ EigStatic es;
     __shared__ int sgn[ZS_MAXM];
     EigWork<T, REF> w;
-    eig_carve<T, REF>(dsm, c.n, m, w);
+    eig_carve<T, REF>(dsm, c.n, m, yglob != 0, ws, w);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = blockIdx.x; j < c.nblk; j += gridDim.x) {
         const int64_t r0 = (int64_t)j * c.b;
@@ -654,7 +742,7 @@ __global__ void __launch_bounds__(256) k_stack(QueryArgs a) {
 
 // Stitched core: top-k_q eigenpairs of M^T M -> Sigma_r, V_r; results S, V.
 template <typename T, bool REF, int MB>
-__global__ void __launch_bounds__(256) k_eig_query(QueryArgs a, int m) {
+__global__ void __launch_bounds__(256) k_eig_query(QueryArgs a, int m, int yglob, void* ws) {
     extern __shared__ __align__(16) char dsm[];
     __shared__ JacobiScratch<T> js;
     __shared__ JacobiScratch<double> jd;
@@ -662,7 +750,7 @@ __global__ void __launch_bounds__(256) k_eig_query(QueryArgs a, int m) {
     __shared__ int sgn[ZS_MAXM];
     __shared__ int s_rank;
     EigWork<T, REF> w;
-    eig_carve<T, REF>(dsm, a.n, m, w);
+    eig_carve<T, REF>(dsm, a.n, m, yglob != 0, ws, w);
     const int tid = threadIdx.x, nt = blockDim.x, n = a.n, kq = a.kq, kout = a.kout;
     const int nq = a.hdr->nq;
     using TR = typename Prec<T, REF>::TR;
@@ -804,31 +892,54 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a, int rows_tile) {
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-int eig_subspace_width(int n, int kq, int extra, bool fp64, bool refine) {
-    if (n <= 64) return n;
-    const bool ref = refine && !fp64;
-    int m = std::min(n, kq + extra);
-    while (m > kq + 2 && eig_smem_bytes(n, m, fp64, ref) > 200 * 1024) --m;
-    if (m > ZS_MAXM) m = ZS_MAXM;
-    if (eig_smem_bytes(n, m, fp64, ref) > 220 * 1024 || m < kq) return -1;
-    return m;
-}
-
-size_t eig_smem_bytes(int n, int m, bool fp64, bool refine) {
+size_t eig_smem_bytes(int n, int m, bool fp64, bool refine, bool yglob) {
     const size_t ts = fp64 ? 8 : 4;
     const bool dense = (m == n && n <= 64);
     const size_t ld = m + 1;
     auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
     size_t s = 0;
-    if (!dense) s += 2 * r16(ts * n * ld);
+    if (!dense) s += (yglob ? 1 : 2) * r16(ts * n * ld);
     s += 2 * r16(ts * m * ld);
     if (refine && !fp64) s += 3 * r16(8 * m * ld);
     return s;
 }
 
+// Subspace width m = kq + p (p = extra, at most 64 columns); the Y block moves
+// to global memory when shared memory cannot hold both n x m blocks.
+EigPlan eig_plan(int n, int kq, int extra, bool fp64, bool refine) {
+    EigPlan p;
+    const bool ref = refine && !fp64;
+    const size_t cap = 200 * 1024;
+    if (n <= 64) {
+        p.m = n;
+        p.yglob = false;
+        p.smem = eig_smem_bytes(n, n, fp64, ref, false);
+        p.ok = p.smem <= cap;
+        return p;
+    }
+    int m = std::min(std::min(n, kq + extra), ZS_MAXM);
+    if (eig_smem_bytes(n, m, fp64, ref, false) <= cap) {
+        p.m = m;
+        p.yglob = false;
+    } else {
+        while (m > kq + 2 && eig_smem_bytes(n, m, fp64, ref, true) > cap) --m;
+        p.m = m;
+        p.yglob = true;
+    }
+    p.smem = eig_smem_bytes(n, p.m, fp64, ref, p.yglob);
+    p.ok = p.smem <= cap && p.m >= kq;
+    return p;
+}
+
+size_t eig_ws_bytes(int n, bool fp64, int ctas) {
+    return (size_t)(fp64 ? 8 : 4) * n * (ZS_MAXM + 1) * std::max(ctas, 1);
+}
+
+// Opt in to the dynamic shared memory a launch needs (static + dynamic may not
+// exceed 48 KB without it).
 template <typename K>
 static cudaError_t set_smem(K kern, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 32 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -843,25 +954,32 @@ static cudaError_t compress_impl(const CompressChunk& c, const Tuning& tu, int n
     const int ntile = (c.n + 63) / 64;
     const int npairs = ntile * (ntile + 1) / 2;
     dim3 gg(npairs, std::min(c.nblk, 65535));
-    k_gram_compress<Tin, T><<<gg, 256, 0, st>>>(c);
+    {
+        prof::Scope ps("gram_compress", st);
+        k_gram_compress<Tin, T><<<gg, 256, 0, st>>>(c);
+    }
     ZS_TRY(cudaGetLastError());
     const bool fp64 = std::is_same<T, double>::value;
-    const int m = eig_subspace_width(c.n, c.k, tu.eig_m_extra, fp64, REF);
-    if (m < 0) return cudaErrorInvalidValue;
-    const size_t sm = eig_smem_bytes(c.n, m, fp64, REF);
-    const int grid_e = std::min(c.nblk, 65535);
-    if (m <= 32) {
-        ZS_TRY(set_smem(k_eig_compress<T, REF, 32>, sm));
-        k_eig_compress<T, REF, 32><<<grid_e, 256, sm, st>>>(c, m);
+    const EigPlan ep = eig_plan(c.n, c.k, tu.eig_m_extra, fp64, REF);
+    if (!ep.ok) return cudaErrorInvalidValue;
+    const int grid_e = std::min(c.nblk, ep.yglob ? c.ews_ctas : 65535);
+    if (ep.m <= 32) {
+        ZS_TRY(set_smem(k_eig_compress<T, REF, 32>, ep.smem));
+        prof::Scope ps("eig_compress", st);
+        k_eig_compress<T, REF, 32><<<grid_e, 256, ep.smem, st>>>(c, ep.m, ep.yglob, c.ews);
     } else {
-        ZS_TRY(set_smem(k_eig_compress<T, REF, 64>, sm));
-        k_eig_compress<T, REF, 64><<<grid_e, 256, sm, st>>>(c, m);
+        ZS_TRY(set_smem(k_eig_compress<T, REF, 64>, ep.smem));
+        prof::Scope ps("eig_compress", st);
+        k_eig_compress<T, REF, 64><<<grid_e, 256, ep.smem, st>>>(c, ep.m, ep.yglob, c.ews);
     }
     ZS_TRY(cudaGetLastError());
     const size_t smu = sizeof(T) * ((size_t)c.k * (c.n + 1) + 32 * (size_t)(c.n + 1) + c.k) + 64;
     ZS_TRY(set_smem(k_form_u<Tin, T>, smu));
     dim3 gu(std::min((c.b + 31) / 32, 8), std::min(c.nblk, 65535));
-    k_form_u<Tin, T><<<gu, 256, smu, st>>>(c);
+    {
+        prof::Scope ps("form_u", st);
+        k_form_u<Tin, T><<<gu, 256, smu, st>>>(c);
+    }
     ZS_TRY(cudaGetLastError());
     note_launches(3);
     (void)num_sms;
@@ -892,35 +1010,42 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
         size_t sm = 2 * r16(sizeof(T) * k * ld) + r16(sizeof(T) * 64 * ld);
         if (REF) sm += 3 * r16(sizeof(double) * k * ld);
         ZS_TRY(set_smem(k_partial<T, REF>, sm));
+        prof::Scope ps("partial_svd", st);
         k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
-    k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
+    {
+        prof::Scope ps("stack", st);
+        k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
+    }
     ZS_TRY(cudaGetLastError());
     {
         const int ntile = (n + 63) / 64;
         const int npairs = ntile * (ntile + 1) / 2;
         dim3 gg(npairs, std::min(max_nq, 65535));
+        prof::Scope ps("gram_query", st);
         k_gram_query<T><<<gg, 256, 0, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
     {
-        const int m = eig_subspace_width(n, kq, tu.eig_m_extra, fp64, REF);
-        if (m < 0) return cudaErrorInvalidValue;
-        const size_t sm = eig_smem_bytes(n, m, fp64, REF);
-        const int grid = std::min(max_nq, 65535);
-        if (m <= 32) {
-            ZS_TRY(set_smem(k_eig_query<T, REF, 32>, sm));
-            k_eig_query<T, REF, 32><<<grid, 256, sm, st>>>(a, m);
+        const EigPlan ep = eig_plan(n, kq, tu.eig_m_extra, fp64, REF);
+        if (!ep.ok) return cudaErrorInvalidValue;
+        const int grid = std::min(max_nq, ep.yglob ? a.ews_ctas : 65535);
+        if (ep.m <= 32) {
+            ZS_TRY(set_smem(k_eig_query<T, REF, 32>, ep.smem));
+            prof::Scope ps("eig_query", st);
+            k_eig_query<T, REF, 32><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
         } else {
-            ZS_TRY(set_smem(k_eig_query<T, REF, 64>, sm));
-            k_eig_query<T, REF, 64><<<grid, 256, sm, st>>>(a, m);
+            ZS_TRY(set_smem(k_eig_query<T, REF, 64>, ep.smem));
+            prof::Scope ps("eig_query", st);
+            k_eig_query<T, REF, 64><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
         }
         ZS_TRY(cudaGetLastError());
     }
     {
         const size_t sm = sizeof(T) * ((size_t)kq * (n + 1) + (size_t)k * (n + 1) + (size_t)k * kq + (size_t)k * k) + 64;
         ZS_TRY(set_smem(k_ur<T>, sm));
+        prof::Scope ps("stitched_u", st);
         k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
@@ -928,6 +1053,7 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
         const int rt = tu.lift_rows;
         const size_t sm = sizeof(T) * ((size_t)k * kq + (size_t)rt * (k + 1)) + 64;
         ZS_TRY(set_smem(k_lift<T>, sm));
+        prof::Scope ps("lift", st);
         k_lift<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, sm, st>>>(a, rt);
         ZS_TRY(cudaGetLastError());
     }

@@ -56,6 +56,7 @@ SIGNATURES = {
     "zs_store_create": (C.c_int, [C.POINTER(StoreConfig), C.POINTER(C.c_void_p)]),
     "zs_store_destroy": (None, [C.c_void_p]),
     "zs_store_append": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
+    "zs_store_reset": (C.c_int, [C.c_void_p]),
     "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "zs_store_export_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
@@ -71,6 +72,10 @@ SIGNATURES = {
     "zs_status_str": (C.c_char_p, [C.c_int]),
     "zs_last_error": (C.c_char_p, []),
     "zs_launch_count": (C.c_int64, []),
+    "zs_profile_enable": (None, [C.c_int32]),
+    "zs_profile_reset": (None, []),
+    "zs_profile_count": (C.c_int32, []),
+    "zs_profile_get": (C.c_int, [C.c_int32, C.POINTER(C.c_char_p), C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
 }
 
 
@@ -169,6 +174,9 @@ class Store:
         on_dev = 1 if t.is_cuda else 0
         _check(lib().zs_store_append(self._h, t.data_ptr(), t.shape[0], t.stride(0), on_dev, _stream_ptr(stream)))
 
+    def reset(self):
+        _check(lib().zs_store_reset(self._h))
+
     def info(self):
         T, nb, by = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib().zs_store_info(self._h, C.byref(T), C.byref(nb), C.byref(by)))
@@ -252,3 +260,21 @@ class Server:
 
 def launch_count() -> int:
     return int(lib().zs_launch_count())
+
+
+def profile(on: bool = True):
+    lib().zs_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().zs_profile_reset()
+
+
+def profile_table() -> dict:
+    """{kernel name: (launches, total device ms)} of the launches profiled so far."""
+    out = {}
+    for i in range(lib().zs_profile_count()):
+        name, n, ms = C.c_char_p(), C.c_int64(), C.c_double()
+        _check(lib().zs_profile_get(i, C.byref(name), C.byref(n), C.byref(ms)))
+        out[name.value.decode()] = (n.value, ms.value)
+    return out

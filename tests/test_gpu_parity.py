@@ -14,7 +14,7 @@ from tests._parity import compare_query, gpu_store, sigma_rel_err, _to_np
 
 pytestmark = pytest.mark.gpu
 
-F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-12)
+F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-10)
 F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=1e-4)
 
 
