@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 range-SVD hot path (storage phase + query phase).
+
+One step = one pass of the whole hot path over one synthetic workload:
+  (1) compress every block of the T x n matrix (already resident in HBM) into
+      the store: Gram, eigen core, U  (Section 3.2, Algorithm 1);
+  (2) answer a batch of range queries from the store: Partial-SVD, stack,
+      stitched core, lift  (Section 3.3, Algorithms 2-3).
+`value` is the storage-phase throughput in GB/s of input (the compression
+target of the workload); queries/s of the batch is reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W --workload NAME]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+
+Under torchrun each rank runs its own replica of the workload on its GPU
+(weak scaling, no data-path collective); timings are max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "range-SVD queries/s, p50/p99 ms, compress GB/s vs HBM peak, at fixed rel error"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _input_rows(w, host=False):
+    A = synthetic.rows(w.series, dtype=np.float64)
+    if w.dtype == "f64":
+        return A
+    if w.dtype == "f32":
+        return A.astype(np.float32)
+    return synthetic.to_bf16_bits(A).view(np.int16)
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (reference arm / cpu_baseline)
+# ----------------------------------------------------------------------------
+def oracle_sample(w, budget_s: float, rng_seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload: compress the
+    first blocks until about budget_s/2 has passed, then answer queries drawn
+    over the compressed sample for the rest.  Returns a dict of rates."""
+    import oracle
+    try:
+        import threadpoolctl
+        cores = max(p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    b, n, k = w.b, w.series.n, w.k
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    # compress blocks one by one (bounded)
+    blocks, nb, tc = [], 0, 0.0
+    nb_max = w.series.T // b
+    while nb < nb_max and tc < budget_s / 2:
+        A = synthetic.rows(w.series, nb * b, (nb + 1) * b)
+        if w.dtype == "f32":
+            A = A.astype(np.float32).astype(np.float64)
+        elif w.dtype == "bf16":
+            A = synthetic.bf16_bits_to_f64(synthetic.to_bf16_bits(A))
+        tb = time.perf_counter()
+        blocks.append(oracle.compress_block(A, k))   # only the oracle's work is timed
+        tc += time.perf_counter() - tb
+        nb += 1
+    st = oracle.Store(b=b, n=n, k=k, T=nb * b, U=[x[0] for x in blocks], s=[x[1] for x in blocks],
+                      Vt=[x[2] for x in blocks])
+    T = nb * b
+    ts, te = synthetic.queries(T, 10_000, min(w.lmin or 1_000, T), min(w.lmax or T, T), seed=rng_seed)
+    t1 = time.perf_counter()
+    nq = 0
+    while nq < len(ts) and time.perf_counter() - t1 < budget_s / 2:
+        oracle.query(st, int(ts[nq]), int(te[nq]))
+        nq += 1
+    tq = time.perf_counter() - t1
+    return {"compress_gbps": nb * b * n * itemsize / max(tc, 1e-9) / 1e9, "blocks": nb,
+            "queries_per_s": nq / max(tq, 1e-9), "queries": nq, "cores": cores,
+            "compress_s": tc, "query_s": tq}
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    per_step = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(w, args.ref_budget, rng_seed=i)
+        if i >= args.warmup:
+            per_step.append(r)
+        last = r
+    v = statistics.mean(r["compress_gbps"] for r in per_step)
+    sample = (f"per step: oracle compresses the first {last['blocks']} blocks of {w.b}x{w.series.n} "
+              f"and answers {last['queries']} queries over them (~{args.ref_budget:.0f} s of CPU)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "T": w.series.T, "n": w.series.n, "b": w.b, "k": w.k,
+                       "input_dtype": w.dtype},
+            "queries_per_s": statistics.mean(r["queries_per_s"] for r in per_step),
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": last["cores"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def kernel_model(name, w, launches_per_step, nq_total_rows):
+    """Algorithmic work per launch of a kernel, for the roofline object."""
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    T, n, b, k = w.series.T, w.series.n, w.b, w.k
+    if name in ("gram_compress", "form_u"):
+        # every input byte read once per launch set
+        return "hbm", T * n * itemsize / launches_per_step
+    if name == "lift":
+        # read U rows (k) and write output rows (k_out = k), factor type 4 B
+        return "hbm", nq_total_rows * 2 * k * 4 / launches_per_step
+    return None, None
+
+
+def run_gpu(args, w):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_00754_gb300 as zs
+    from paper_1805_00754_gb300 import zoomsvd
+
+    T, n, b, k = w.series.T, w.series.n, w.b, w.k
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    A = _input_rows(w)
+    rows_dev = torch.from_numpy(A).to(f"cuda:{local}")
+    in_bytes = T * n * itemsize
+    nq = args.nq if args.nq is not None else w.nq
+    ts, te = synthetic.queries(T, nq, w.lmin, w.lmax, seed=synthetic.SEED_BASE + 99)
+    st = zs.Store(n=n, b=b, k=k, dtype=w.dtype, capacity_rows=T, device=local,
+                  fp64_refine=(w.dtype == "bf16"))
+    outs = [st.new_result(int(a), int(z), k) for a, z in zip(ts, te)]
+    out_rows = int(np.sum(te - ts + 1))
+    stream = torch.cuda.current_stream()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def step(e=None):
+        st.reset()
+        if e:
+            e[0].record(stream)
+        st.append(rows_dev)
+        if e:
+            e[1].record(stream)
+        if nq:
+            st.query_batch(ts, te, k, outs=outs)
+        if e:
+            e[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    zoomsvd.profile(True)
+    zoomsvd.profile_reset()
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = zs.launch_count()
+    for i in range(args.steps):
+        step(ev[i])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = zs.launch_count() - l0
+    clk = clocks.stop()
+    table = zoomsvd.profile_table()
+    zoomsvd.profile(False)
+    tc = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    tq = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    times = torch.tensor([tc, tq], dtype=torch.float64, device=f"cuda:{local}")
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    tc, tq = times.tolist()
+    K = args.steps
+    compress_gbps = ws * K * in_bytes / tc / 1e9
+    qps = ws * K * nq / tq if nq else None
+    ms_step = (tc + tq) / K * 1e3
+
+    # e2e through the C ABI from pinned host rows (H2D inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(A).pin_memory()
+        sig_host = torch.empty((k,), dtype=st.fdtype).pin_memory()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        te2e = 0.0
+        for i in range(args.warmup + K):
+            st.reset()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            st.append(host)
+            _, s_dev, _, _ = st.export_block((T - 1) // b)
+            sig_host.copy_(s_dev, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if i >= args.warmup:
+                te2e += e0.elapsed_time(e1) / 1e3
+        tt = torch.tensor([te2e], dtype=torch.float64, device=f"cuda:{local}")
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * K * in_bytes / tt.item() / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": k * (8 if w.dtype == "f64" else 4)}
+
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    dom = max(table.items(), key=lambda kv: kv[1][1]) if table else None
+    roof = None
+    if dom:
+        name, (nl, ms) = dom
+        per_step = nl / K
+        bound, units = kernel_model(name, w, per_step, out_rows)
+        avg_s = ms / nl / 1e3
+        if bound == "hbm":
+            ach = units / avg_s / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                    "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
+        else:
+            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
+    kernels = {nm: {"launches": v[0], "ms_per_step": v[1] / K} for nm, v in table.items()}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        r = oracle_sample(w, args.cpu_budget)
+        cpu = {"value": r["compress_gbps"], "unit": "GB/s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"oracle compressed the first {r['blocks']} blocks ({r['compress_s']:.1f} s) and answered "
+                         f"{r['queries']} queries over them ({r['query_s']:.1f} s); queries/s "
+                         f"{r['queries_per_s']:.3g}"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": compress_gbps, "unit": "GB/s", "n_gpus": ws, "steps": K,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"f64": "f64", "f32": "f32", "bf16": "bf16-in/f32"}[w.dtype],
+                "data": "synthetic",
+                "config": {"workload": w.name, "T": T, "n": n, "b": b, "k": k, "input_dtype": w.dtype,
+                           "queries_per_step": nq, "query_rows_per_step": out_rows,
+                           "l2": "inputs larger than L2 (no flush needed)",
+                           "parallelism": f"replicas x{ws}"},
+                "queries_per_s": qps, "compress_s_per_step": tc / K, "query_s_per_step": tq / K,
+                "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"],
+                "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    st.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="compress_f32", choices=sorted(synthetic.WORKLOADS))
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-budget", type=float, default=6.0)
+    args = ap.parse_args()
+    w = synthetic.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()
