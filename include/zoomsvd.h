@@ -131,6 +131,32 @@ zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
 zs_status zs_store_export_block(const zs_store* st, int64_t i, void* U, void* sigma, void* Vt,
                                 int32_t* rows_i, int32_t* k_i, void* stream);
 
+/* Storage-phase compression that allocates nothing (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory: code
+ * running while a CUDA graph is being captured, plug-ins whose host program
+ * owns every device allocation through its own pool, or loops that must
+ * never enter the allocator).  Compresses nrows device rows (row stride
+ * ld >= n elements of in_dtype) into ceil(nrows / b) blocks exactly as
+ * zs_store_append does, without a store: block j's factors go to caller
+ * device buffers U + j*b*k (b x k, ld k; rows past a short last block are
+ * zero), sigma + j*k (k) and Vt + j*k*n (k x n, ld n), in the factor type
+ * (double for ZS_F64 input, else float).  flags takes ZS_FLAG_FP64_REFINE.
+ * Its scratch is one fixed 32 MiB device array inside the library (held on
+ * every device that loads the library until the process exits): the
+ * per-block n x n Gram matrices of a chunk of blocks plus, for large n, the
+ * eigen core's workspace.  n whose per-block scratch does not fit is
+ * rejected with ZS_EINVAL; the call makes no cudaMalloc, cudaFree or other
+ * allocating call.  Every call uses the same array and overwrites the parts
+ * it reads before reading them (nothing has to start at zero), so calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it; make that first call before any
+ * stream capture.  Work is enqueued on `stream`.                           */
+zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_t ld, int32_t in_dtype, int64_t n,
+                              int64_t b, int32_t k, int32_t flags, void* U, void* sigma, void* Vt,
+                              void* stream);
+
 /* ------------------------------------------------------------------------
  * Query phase (Algorithm 2 with Partial-SVD Algorithm 3; Eq. 5-9).
  * ------------------------------------------------------------------------ */

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libzoomsvd.so")
 
-SOURCES = ["zs_kernels.cu", "zs_api.cu", "zs_serve.cpp"]
+SOURCES = ["zs_kernels.cu", "zs_api.cu", "zs_serve.cpp", "zs_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

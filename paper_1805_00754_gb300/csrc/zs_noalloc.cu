@@ -1,0 +1,115 @@
+// zs_noalloc.cu - storage-phase compression that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
+// being captured, plug-ins living inside a host application that owns every
+// device allocation through its own pool, or latency-critical loops that must
+// never enter the driver's allocator.  For them zs_compress_noalloc runs the
+// same storage-phase kernels as zs_store_append, but their scratch (the n x n
+// Gram matrix of each block and, for large n, the eigen core's subspace block)
+// lives in one file-scope device array of fixed size instead of memory the
+// library allocates.  The caller supplies the input rows and the output
+// factor buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "zoomsvd.h"
+#include "zs_api_internal.h"
+#include "zs_internal.h"
+
+namespace {
+
+// Fixed scratch, resident on every device that loads this library until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the array, looked up once per device (host code may not use
+// the symbol itself as a device pointer).
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mu;
+void* g_addr[kMaxDevices] = {nullptr};
+
+zs_status scratch_address(int dev, void** out) {
+    if (dev < 0 || dev >= kMaxDevices) return zs::fail(ZS_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_addr_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return ZS_OK;
+}
+
+}  // namespace
+
+extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_t ld, int32_t in_dtype, int64_t n,
+                                         int64_t b, int32_t k, int32_t flags, void* U, void* sigma, void* Vt,
+                                         void* stream) {
+    if (in_dtype != ZS_F64 && in_dtype != ZS_F32 && in_dtype != ZS_BF16)
+        return zs::fail(ZS_EDTYPE, "unknown in_dtype %d", in_dtype);
+    if (n < 1 || n > 1024 || b < 1 || b > ((int64_t)1 << 24) || k < 1 || k > 64 || k > n || nrows < 0 || ld < n)
+        return zs::fail(ZS_EINVAL, "bad sizes (n=%lld b=%lld k=%d nrows=%lld ld=%lld)", (long long)n, (long long)b,
+                        k, (long long)nrows, (long long)ld);
+    if (nrows == 0) return ZS_OK;
+    if (!rows || !U || !sigma || !Vt) return zs::fail(ZS_EINVAL, "null pointer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetDevice");
+    void* scratch = nullptr;
+    zs_status s = scratch_address(dev, &scratch);
+    if (s != ZS_OK) return s;
+    int num_sms = 1;
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "cudaDeviceGetAttribute");
+
+    const bool fp64 = (in_dtype == ZS_F64);
+    const bool ref = (flags & ZS_FLAG_FP64_REFINE) && !fp64;
+    const zs::Tuning tune;
+    const zs::EigPlan ep = zs::eig_plan((int)n, k, tune.eig_m_extra, fp64, ref);
+    if (!ep.ok) return zs::fail(ZS_EINVAL, "n=%lld with k=%d does not fit the eigen core", (long long)n, k);
+    const size_t ts = fp64 ? 8 : 4;
+    const size_t insize = in_dtype == ZS_F64 ? 8 : (in_dtype == ZS_F32 ? 4 : 2);
+    // carve: [eigen workspace | Gram matrices of one chunk of blocks]
+    int ews_ctas = 0;
+    size_t ews_bytes = 0;
+    if (ep.yglob) {
+        ews_ctas = std::max(1, num_sms);
+        while (ews_ctas > 1 && zs::eig_ws_bytes((int)n, fp64, ews_ctas) > kNoAllocScratchBytes / 2) ews_ctas /= 2;
+        ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
+    }
+    const size_t gper = ts * (size_t)n * n;
+    if (ews_bytes + gper > kNoAllocScratchBytes)
+        return zs::fail(ZS_EINVAL, "n=%lld needs %zu scratch bytes per block; the no-alloc scratch holds %zu",
+                        (long long)n, ews_bytes + gper, kNoAllocScratchBytes);
+    const int chunk = (int)std::min<size_t>((kNoAllocScratchBytes - ews_bytes) / gper, 65535);
+    const int64_t nblk = (nrows + b - 1) / b;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t j0 = 0; j0 < nblk; j0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, nblk - j0);
+        zs::CompressChunk ch;
+        memset(&ch, 0, sizeof ch);
+        ch.A = (const char*)rows + (size_t)j0 * b * ld * insize;
+        ch.lda = ld;
+        ch.rows_total = std::min<int64_t>(nrows - j0 * b, (int64_t)nb * b);
+        ch.nblk = nb;
+        ch.slot0 = 0;
+        ch.b = (int32_t)b;
+        ch.n = (int32_t)n;
+        ch.k = k;
+        ch.in_kind = in_dtype;
+        ch.G = (char*)scratch + ews_bytes;
+        ch.ews = ep.yglob ? scratch : nullptr;
+        ch.ews_ctas = ews_ctas;
+        ch.U = (char*)U + ts * (size_t)j0 * b * k;
+        ch.sig = (char*)sigma + ts * (size_t)j0 * k;
+        ch.vt = (char*)Vt + ts * (size_t)j0 * k * n;
+        e = zs::launch_compress(ch, fp64, flags, tune, num_sms, st);
+        if (e != cudaSuccess) return zs::cuda_fail(e, "compression kernels");
+    }
+    return ZS_OK;
+}
