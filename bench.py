@@ -188,7 +188,7 @@ def kernel_model(name, w, launches_per_step, nq_total_rows):
     """Algorithmic work per launch of a kernel, for the roofline object."""
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
     T, n, b, k = w.series.T, w.series.n, w.b, w.k
-    if name in ("gram_compress", "form_u"):
+    if name in ("gram_compress", "form_u", "gram_lo", "project"):
         # every input byte read once per launch set
         return "hbm", T * n * itemsize / launches_per_step
     if name == "lift":

@@ -56,7 +56,12 @@ enum {
     /* Re-solve each small eigen core (k x k, Rayleigh-Ritz m x m) in FP64
      * after the FP32 Jacobi sweeps: FP64-accumulated Rayleigh quotient and one
      * FP64 Jacobi refinement sweep.  No effect on ZS_F64 stores (all FP64).  */
-    ZS_FLAG_FP64_REFINE = 1
+    ZS_FLAG_FP64_REFINE = 1,
+    /* Compute every Gram matrix exactly in FP32 on the CUDA cores (slower)
+     * instead of the default for float stores with n >= 128: a bf16
+     * tensor-core Gram that only locates the dominant subspace, followed by a
+     * split-bf16 (~FP32) projection and Rayleigh-Ritz that sets the accuracy. */
+    ZS_FLAG_EXACT_GRAM = 2
 };
 
 typedef struct zs_store zs_store;

@@ -68,7 +68,7 @@ void QueryExec::release() {
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     auto fh = [](void*& p) { if (p) cudaFreeHost(p); p = nullptr; };
     if (done) { cudaEventSynchronize(done); cudaEventDestroy(done); done = nullptr; }
-    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C); f(ews);
+    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C); f(ews); f(qb); f(ys);
     fh(h_blob);
     cap_nq = 0;
     cap_slabs = 0;
@@ -103,6 +103,11 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
     if ((s = al(&C, ts * want_sl * k * want_kq, "lift coeff")) != ZS_OK) return s;
     ews_ctas = std::max(1, st.num_sms);
     if ((s = al(&ews, eig_ws_bytes((int)n, st.fp64, ews_ctas), "eigen workspace")) != ZS_OK) return s;
+    if (use_tc_path(st.fp64, (int)n, st.cfg.flags)) {
+        const size_t m = tc_width(want_kq, st.tune.eig_m_extra);
+        if ((s = al(&qb, 2 * m * (size_t)n * want_nq, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&ys, 4 * m * (size_t)want_sl * k, "projections")) != ZS_OK) return s;
+    }
     cap_nq = want_nq;
     cap_slabs = want_sl;
     cap_kq = want_kq;
@@ -112,8 +117,9 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
 size_t QueryExec::bytes_for(const zs_store& st, int nq, int64_t nslab, int kq) {
     const size_t ts = st.tsize;
     const size_t n = st.cfg.n, k = st.cfg.k;
+    const size_t m = 64;
     return ts * (nslab * k * n + (size_t)nq * n * n + (size_t)nq * kq * (n + 1) + 2 * (size_t)nq * k * k +
-                 nslab * k * kq) + sizeof(QPlan) * nq;
+                 nslab * k * kq + nslab * k * m + (size_t)nq * n * m / 2) + sizeof(QPlan) * nq;
 }
 
 // ---------------------------------------------------------------------------
@@ -201,7 +207,11 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.C = x.C;
     a.ews = x.ews;
     a.ews_ctas = x.ews_ctas;
-    cudaError_t e = launch_query(a, st.fp64, nq, nslab, st.tune, st.num_sms, stream);
+    a.qb = x.qb;
+    a.ys = x.ys;
+    int max_rows = 0;
+    for (const QPlan& P : plans) max_rows = std::max(max_rows, P.nslab * (int)st.cfg.k);
+    cudaError_t e = launch_query(a, st.fp64, nq, nslab, max_rows, st.cfg.flags, st.tune, st.num_sms, stream);
     if (e != cudaSuccess) return cuda_fail(e, "query kernels");
     ZS_CU(cudaEventRecord(x.done, stream), "event record");
     return ZS_OK;
@@ -233,6 +243,11 @@ static zs_status store_alloc(zs_store* st) {
     const size_t gper = ts * (size_t)c.n * c.n;
     st->gchunk = (int)std::max<size_t>(1, std::min<size_t>(st->gram_budget / gper, 65535));
     if ((s = al(&st->gscr, gper * st->gchunk, "gram scratch")) != ZS_OK) return s;
+    if (use_tc_path(st->fp64, (int)c.n, c.flags)) {
+        const size_t m = tc_width(c.k, st->tune.eig_m_extra);
+        if ((s = al(&st->qb, 2 * m * (size_t)c.n * st->gchunk, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&st->ys, 4 * m * (size_t)c.b * st->gchunk, "projections")) != ZS_OK) return s;
+    }
     st->ews_ctas = std::max(1, st->num_sms);
     if ((s = al(&st->ews, eig_ws_bytes((int)c.n, st->fp64, st->ews_ctas), "eigen workspace")) != ZS_OK) return s;
     // host staging: two device buffers of whole blocks
@@ -299,6 +314,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     st->qx.release();
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     f(st->U); f(st->sig); f(st->vt); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
+    f(st->qb); f(st->ys);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
@@ -334,6 +350,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.vt = st->vt;
         ch.ews = st->ews;
         ch.ews_ctas = st->ews_ctas;
+        ch.qb = st->qb;
+        ch.ys = st->ys;
         cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, stream);
         if (e != cudaSuccess) return cuda_fail(e, "compression kernels");
     }

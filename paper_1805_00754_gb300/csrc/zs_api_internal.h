@@ -23,6 +23,8 @@ struct QueryExec {
     void *M = nullptr, *G = nullptr, *sr = nullptr, *vr = nullptr, *tco = nullptr, *C = nullptr;
     void* ews = nullptr;
     int ews_ctas = 1;
+    void* qb = nullptr;
+    void* ys = nullptr;
     cudaEvent_t done = nullptr;   // last batch that used this scratch
     ~QueryExec();
     void release();
@@ -56,6 +58,8 @@ struct zs_store {
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace
     int ews_ctas = 1;
+    void* qb = nullptr;            // tensor path: subspace bases (gchunk x n x m bf16)
+    void* ys = nullptr;            // tensor path: projections (gchunk x b x m float)
     int gchunk = 1;
     size_t gram_budget = (size_t)64 << 20;
     void* stage[2] = {nullptr, nullptr};

@@ -34,6 +34,8 @@ struct CompressChunk {
     void* vt;         // store: k * n per slot
     void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
     int32_t ews_ctas;
+    void* qb;         // tensor path: nblk x n x 64 bf16 subspace bases
+    void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).
@@ -85,6 +87,8 @@ struct QueryArgs {
     void* C;          // nslab_total * k * kq    lift coefficients per slab
     void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
     int32_t ews_ctas;
+    void* qb;         // tensor path: nq x n x 64 bf16 subspace bases
+    void* ys;         // tensor path: nslab_total x k x 64 floats (Y = M Q~)
 };
 
 // Launch configuration chosen by the autotuner (or defaults).
@@ -93,14 +97,24 @@ struct Tuning {
     int lift_rows = 64;          // rows staged per lift tile
     int slab_ctas_per_sm = 4;    // persistent grid for slab work lists
     int eig_m_extra = 16;        // subspace oversampling p (m = kq + p)
+    int power_its = 1;           // tensor path: power steps on the bf16 Gram
 };
+
+// The tensor-core path (bf16 Gram for the subspace, split-bf16 projection and
+// Rayleigh-Ritz for accuracy) serves float factor stores with n >= 128 unless
+// the store asks for the exact FP32 Gram.
+inline bool use_tc_path(bool fp64, int n, int flags) { return !fp64 && n >= 128 && !(flags & 2); }
+inline int tc_width(int kq, int extra) {
+    int m = ((kq + extra) + 7) / 8 * 8;
+    return m > 64 ? 64 : m;
+}
 
 // Launchers (zs_kernels.cu).  All enqueue on `st` and return cudaError_t of the
 // launch.  `fp64` selects the double-precision instantiation (F64 store).
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu,
                             int num_sms, cudaStream_t st);
-cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs,
-                         const Tuning& tu, int num_sms, cudaStream_t st);
+cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, int max_rows,
+                         int flags, const Tuning& tu, int num_sms, cudaStream_t st);
 struct EigPlan {
     int m = 0;          // subspace width (n for the dense path)
     bool yglob = false; // Y block in global workspace

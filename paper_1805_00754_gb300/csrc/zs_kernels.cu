@@ -889,6 +889,12 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a, int rows_tile) {
     }
 }
 
+}  // namespace zs
+
+#include "zs_tc_kernels.cuh"
+
+namespace zs {
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -986,9 +992,80 @@ static cudaError_t compress_impl(const CompressChunk& c, const Tuning& tu, int n
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core path (see zs_tc_kernels.cuh).
+// ---------------------------------------------------------------------------
+static size_t tc_subspace_smem(int n, int m, bool& yglob) {
+    const size_t both = (size_t)2 * n * (m + 1) * 4;
+    yglob = both > 110 * 1024;
+    return yglob ? (size_t)n * (m + 1) * 4 : both;
+}
+static size_t tc_project_smem(int n, int m) {
+    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)2 * 128 * 72 * 2;
+}
+static size_t tc_rr_smem(int m, bool ref) {
+    return (size_t)4 * m * (m + 1) * (ref ? 8 : 4) + (size_t)2 * m * (m + 1) * 4;
+}
+
+template <class Src, typename Tin, bool REF, bool QUERY>
+static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int max_rows,
+                           int ews_ctas, cudaStream_t st) {
+    const int ntile = (n + 127) / 128;
+    const int npairs = ntile * (ntile + 1) / 2;
+    const int gi = std::min(max_items, 65535);
+    {
+        prof::Scope ps(QUERY ? "gram_lo_query" : "gram_lo", st);
+        k_gram_lo<Src, Tin><<<dim3(npairs, gi), 256, 0, st>>>(src, sc, n);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        bool yglob;
+        const size_t sm = tc_subspace_smem(n, sc.m, yglob);
+        ZS_TRY(set_smem(k_subspace<Src>, sm));
+        prof::Scope ps(QUERY ? "subspace_query" : "subspace", st);
+        k_subspace<Src><<<std::min(gi, yglob ? ews_ctas : 65535), 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        const size_t sm = tc_project_smem(n, sc.m);
+        ZS_TRY(set_smem(k_project<Src, Tin>, sm));
+        prof::Scope ps(QUERY ? "project_query" : "project", st);
+        k_project<Src, Tin><<<dim3((max_rows + 127) / 128, gi), 256, sm, st>>>(src, sc, n);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        const size_t sm = tc_rr_smem(sc.m, REF);
+        ZS_TRY(set_smem(k_rr<Src, REF, QUERY>, sm));
+        prof::Scope ps(QUERY ? "rr_query" : "rr", st);
+        k_rr<Src, REF, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
+    }
+    ZS_TRY(cudaGetLastError());
+    note_launches(4);
+    return cudaSuccess;
+}
+
+template <typename Tin, bool REF>
+static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, cudaStream_t st) {
+    TcScratch sc;
+    sc.G = (float*)c.G;
+    sc.Qb = (__nv_bfloat16*)c.qb;
+    sc.Y = (float*)c.ys;
+    sc.ews = c.ews;
+    sc.ews_ctas = std::max(1, c.ews_ctas);
+    sc.m = tc_width(c.k, tu.eig_m_extra);
+    sc.power_its = tu.power_its;
+    SrcCompress src{c};
+    return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk, c.b, sc.ews_ctas, st);
+}
+
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
                             cudaStream_t st) {
     const bool ref = (flags & 1) != 0;
+    if (use_tc_path(fp64, c.n, flags)) {
+        if (c.in_kind == IN_BF16)
+            return ref ? compress_tc<__nv_bfloat16, true>(c, tu, st) : compress_tc<__nv_bfloat16, false>(c, tu, st);
+        return ref ? compress_tc<float, true>(c, tu, st) : compress_tc<float, false>(c, tu, st);
+    }
     if (fp64) return compress_impl<double, double, false>(c, tu, num_sms, st);
     if (c.in_kind == IN_BF16)
         return ref ? compress_impl<__nv_bfloat16, float, true>(c, tu, num_sms, st)
@@ -998,11 +1075,12 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
 }
 
 template <typename T, bool REF>
-static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs, const Tuning& tu,
-                              int num_sms, cudaStream_t st) {
+static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs, int max_rows, int flags,
+                              const Tuning& tu, int num_sms, cudaStream_t st) {
     const bool fp64 = std::is_same<T, double>::value;
     const int k = a.k, n = a.n, kq = a.kq;
     const int pers = std::max(1, num_sms * tu.slab_ctas_per_sm);
+    const bool tc = use_tc_path(fp64, n, flags);
     // Partial-SVD
     {
         const int ld = k + 1;
@@ -1019,6 +1097,37 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
         k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
     }
     ZS_TRY(cudaGetLastError());
+    if constexpr (!std::is_same<T, double>::value) {
+        if (tc) {
+            TcScratch sc;
+            sc.G = (float*)a.G;
+            sc.Qb = (__nv_bfloat16*)a.qb;
+            sc.Y = (float*)a.ys;
+            sc.ews = a.ews;
+            sc.ews_ctas = std::max(1, a.ews_ctas);
+            sc.m = tc_width(kq, tu.eig_m_extra);
+            sc.power_its = tu.power_its;
+            SrcQuery src{a};
+            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, max_rows, sc.ews_ctas, st)));
+            {
+                const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
+                ZS_TRY(set_smem(k_bfix, sm));
+                prof::Scope ps("boundary_fix", st);
+                k_bfix<<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+                ZS_TRY(cudaGetLastError());
+            }
+            {
+                const int rt = tu.lift_rows;
+                const size_t sm = sizeof(T) * ((size_t)k * kq + (size_t)rt * (k + 1)) + 64;
+                ZS_TRY(set_smem(k_lift<T>, sm));
+                prof::Scope ps("lift", st);
+                k_lift<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, sm, st>>>(a, rt);
+                ZS_TRY(cudaGetLastError());
+            }
+            note_launches(4);
+            return cudaSuccess;
+        }
+    }
     {
         const int ntile = (n + 63) / 64;
         const int npairs = ntile * (ntile + 1) / 2;
@@ -1061,11 +1170,11 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
     return cudaSuccess;
 }
 
-cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, const Tuning& tu,
-                         int num_sms, cudaStream_t st) {
-    if (fp64) return query_impl<double, false>(a, max_nq, max_slabs, tu, num_sms, st);
-    return a.fp64_refine ? query_impl<float, true>(a, max_nq, max_slabs, tu, num_sms, st)
-                         : query_impl<float, false>(a, max_nq, max_slabs, tu, num_sms, st);
+cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, int max_rows, int flags,
+                         const Tuning& tu, int num_sms, cudaStream_t st) {
+    if (fp64) return query_impl<double, false>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st);
+    return a.fp64_refine ? query_impl<float, true>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st)
+                         : query_impl<float, false>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st);
 }
 
 }  // namespace zs

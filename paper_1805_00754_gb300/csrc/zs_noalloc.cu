@@ -82,11 +82,22 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         while (ews_ctas > 1 && zs::eig_ws_bytes((int)n, fp64, ews_ctas) > kNoAllocScratchBytes / 2) ews_ctas /= 2;
         ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
     }
-    const size_t gper = ts * (size_t)n * n;
-    if (ews_bytes + gper > kNoAllocScratchBytes)
+    // per block: its Gram matrix and, on the tensor path, its bf16 subspace
+    // basis and projection block
+    const bool tc = zs::use_tc_path(fp64, (int)n, flags);
+    const size_t mt = tc ? (size_t)zs::tc_width(k, tune.eig_m_extra) : 0;
+    if (tc && ews_bytes == 0) {
+        ews_ctas = std::max(1, num_sms);
+        while (ews_ctas > 1 && zs::eig_ws_bytes((int)n, fp64, ews_ctas) > kNoAllocScratchBytes / 4) ews_ctas /= 2;
+        ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
+    }
+    const size_t qper = ((2 * mt * (size_t)n) + 255) & ~(size_t)255;
+    const size_t yper = ((4 * mt * (size_t)b) + 255) & ~(size_t)255;
+    const size_t gper = ((ts * (size_t)n * n) + 255) & ~(size_t)255;
+    if (ews_bytes + gper + qper + yper > kNoAllocScratchBytes)
         return zs::fail(ZS_EINVAL, "n=%lld needs %zu scratch bytes per block; the no-alloc scratch holds %zu",
-                        (long long)n, ews_bytes + gper, kNoAllocScratchBytes);
-    const int chunk = (int)std::min<size_t>((kNoAllocScratchBytes - ews_bytes) / gper, 65535);
+                        (long long)n, ews_bytes + gper + qper + yper, kNoAllocScratchBytes);
+    const int chunk = (int)std::min<size_t>((kNoAllocScratchBytes - ews_bytes) / (gper + qper + yper), 65535);
     const int64_t nblk = (nrows + b - 1) / b;
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t j0 = 0; j0 < nblk; j0 += chunk) {
@@ -103,7 +114,9 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         ch.k = k;
         ch.in_kind = in_dtype;
         ch.G = (char*)scratch + ews_bytes;
-        ch.ews = ep.yglob ? scratch : nullptr;
+        ch.qb = tc ? (char*)scratch + ews_bytes + gper * chunk : nullptr;
+        ch.ys = tc ? (char*)scratch + ews_bytes + (gper + qper) * chunk : nullptr;
+        ch.ews = (ep.yglob || tc) ? scratch : nullptr;
         ch.ews_ctas = ews_ctas;
         ch.U = (char*)U + ts * (size_t)j0 * b * k;
         ch.sig = (char*)sigma + ts * (size_t)j0 * k;
