@@ -312,6 +312,12 @@ def run_gpu(args, w):
                     "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
     kernels = {nm: {"launches": v[0], "ms_per_step": v[1] / K} for nm, v in table.items()}
 
+    acc = None
+    if rank == 0 and not args.skip_accuracy and nq:
+        acc = accuracy_sample(st, w, A)
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = serve_run(args.serve_seconds, local)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         r = oracle_sample(w, args.cpu_budget)
@@ -330,12 +336,117 @@ def run_gpu(args, w):
                            "parallelism": f"replicas x{ws}"},
                 "queries_per_s": qps, "compress_s_per_step": tc / K, "query_s_per_step": tq / K,
                 "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"],
+                "accuracy": acc, "serving": serving,
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     st.close()
     if dist:
         dist.destroy_process_group()
+
+
+def accuracy_sample(st, w, A, nq=4, max_len=20_000, seed=7):
+    """sigma / subspace error of a few GPU query results against the FP64
+    oracle run on the same (dtype-rounded) rows; only the covered blocks are
+    compressed by the oracle."""
+    import oracle
+    import torch
+    T, b, k = w.series.T, w.b, w.k
+    ts, te = synthetic.queries(T, nq, 2 * b, max_len, seed=seed)
+    worst_s, worst_sin = 0.0, 0.0
+    for a, z in zip(ts, te):
+        S, E = int(a) // b, int(z) // b
+        rows = A[S * b: min((E + 1) * b, T)]
+        if w.dtype == "bf16":
+            exact = synthetic.bf16_bits_to_f64(rows.view(np.uint16))
+        else:
+            exact = np.asarray(rows, dtype=np.float64)
+        ost = oracle.compress(exact, b, k)
+        ref = oracle.query(ost, int(a) - S * b, int(z) - S * b)
+        out = st.query(int(a), int(z))
+        torch.cuda.synchronize()
+        s = out.S.cpu().numpy().astype(np.float64)
+        m = ref.s > 0
+        worst_s = max(worst_s, float(np.max(np.abs(s[m] - ref.s[m]) / ref.s[m])))
+        V = out.V.cpu().numpy().astype(np.float64)[:, m]
+        Q1, _ = np.linalg.qr(V)
+        Q2, _ = np.linalg.qr(ref.V[:, m])
+        worst_sin = max(worst_sin, float(np.linalg.norm(Q2 - Q1 @ (Q1.T @ Q2), 2)))
+    return {"sigma_max_rel_err": worst_s, "v_subspace_sin_max": worst_sin, "queries": int(nq),
+            "vs": "FP64 oracle on the same rounded rows"}
+
+
+def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0):
+    """Serving workload: compressed store of the serving shape, Poisson
+    arrivals at rate_hz with lengths log-uniform 1e3..1e6, new blocks
+    appended at 1 block/ms on another stream while queries run."""
+    import torch
+    import paper_1805_00754_gb300 as zs
+    w = synthetic.WORKLOADS["serving_f32"]
+    T, n, b, k = w.series.T, w.series.n, w.b, w.k
+    extra = int(seconds * 1000) + 16                      # blocks appended during the run
+    A = synthetic.rows(w.series, dtype=np.float32)
+    app = synthetic.rows(synthetic.SeriesSpec(extra * b, n, w.series.s, w.series.noise, 0.0,
+                                              w.series.seed + 1), dtype=np.float32)
+    st = zs.Store(n=n, b=b, k=k, dtype="f32", capacity_rows=T + extra * b, device=local)
+    st.append(torch.from_numpy(A).to(f"cuda:{local}"))
+    app_dev = torch.from_numpy(app).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    arrivals = synthetic.poisson_arrivals(rate_hz, seconds, seed=synthetic.SEED_BASE + 5)
+    ts, te = synthetic.queries(T, len(arrivals), w.lmin, w.lmax, seed=synthetic.SEED_BASE + 6)
+    # results go to a ring arena (never read back); a slot is reused only after
+    # its previous request completed
+    arena_rows = 256 << 20
+    arena = torch.empty((arena_rows, k), dtype=torch.float32, device=f"cuda:{local}")
+    SV = torch.empty((4096, k), dtype=torch.float32, device=f"cuda:{local}")
+    VV = torch.empty((4096, n, k), dtype=torch.float32, device=f"cuda:{local}")
+    sv = zs.Server(st, max_batch=512, max_inflight=3, queue_capacity=1 << 16, memory_budget=8 << 30)
+    from paper_1805_00754_gb300 import zoomsvd
+    import ctypes as C
+    app_stream = torch.cuda.Stream(device=f"cuda:{local}")
+    stop = threading.Event()
+
+    def appender():
+        i = 0
+        t0 = time.perf_counter()
+        while not stop.is_set() and i < extra:
+            st.append(app_dev[i * b:(i + 1) * b], stream=app_stream)
+            i += 1
+            nxt = t0 + i * 1e-3
+            d = nxt - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+        return i
+
+    th = threading.Thread(target=appender)
+    pending = []
+    off = 0
+    t_start = time.perf_counter()
+    th.start()
+    lib = zoomsvd.lib()
+    tick = C.c_uint64()
+    for i, t_arr in enumerate(arrivals):
+        d = t_start + t_arr - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        L = int(te[i] - ts[i] + 1)
+        if off + L > arena_rows:
+            off = 0
+        res = zoomsvd.Result(arena.data_ptr() + off * k * 4, k, SV[i % 4096].data_ptr(),
+                             VV[i % 4096].data_ptr(), k, 0)
+        off += L
+        if lib.zs_serve_submit(sv._h, int(ts[i]), int(te[i]), k, C.byref(res), C.byref(tick)) == 0:
+            pending.append(tick.value)
+    for t in pending:
+        sv.wait(t, 120_000)
+    stop.set()
+    th.join()
+    stats = sv.stop()
+    st.close()
+    return {"workload": "serving_f32", "offered_qps": rate_hz, "seconds": seconds,
+            "completed": stats["completed"], "rejected": stats["rejected"],
+            "queries_per_s": stats["queries_per_s"], "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+            "max_ms": stats["max_ms"], "mean_batch": stats["mean_batch"], "appends_per_s": 1000.0}
 
 
 def main():
@@ -350,6 +461,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--skip-accuracy", action="store_true")
     args = ap.parse_args()
     w = synthetic.WORKLOADS[args.workload]
     if args.impl == "reference":

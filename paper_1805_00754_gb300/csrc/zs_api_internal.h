@@ -25,7 +25,16 @@ struct QueryExec {
     int ews_ctas = 1;
     void* qb = nullptr;
     void* ys = nullptr;
+    void* aux = nullptr;
+    int64_t aux_tiles = 0;
     cudaEvent_t done = nullptr;   // last batch that used this scratch
+    // one captured launch set (plan upload + all query kernels) for this
+    // executor's capacity, replayed for every batch that fits it
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_kq = -1, g_kout = -1;
+    int w_kq = -1, w_kout = -1;      // shape of the last eager batch
+    int64_t g_launches = 0;
     ~QueryExec();
     void release();
     zs_status reserve(const zs_store& st, int nq, int64_t nslab, int kq);
@@ -60,12 +69,14 @@ struct zs_store {
     int ews_ctas = 1;
     void* qb = nullptr;            // tensor path: subspace bases (gchunk x n x m bf16)
     void* ys = nullptr;            // tensor path: projections (gchunk x b x m float)
+    void* aux = nullptr;           // tensor path: Rayleigh-Ritz scratch
     int gchunk = 1;
-    size_t gram_budget = (size_t)64 << 20;
+    size_t gram_budget = (size_t)512 << 20;    // per-chunk scratch: Gram + bases + projections
     void* stage[2] = {nullptr, nullptr};
     int stage_blocks = 1;
-    size_t stage_budget = (size_t)64 << 20;
+    size_t stage_budget = (size_t)256 << 20;
     size_t query_budget = (size_t)8 << 30;
+    bool use_graphs = true;        // replay query batches as one captured CUDA graph
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t stage_free[2] = {nullptr, nullptr};
     cudaEvent_t stage_full[2] = {nullptr, nullptr};

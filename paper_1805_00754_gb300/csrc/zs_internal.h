@@ -36,6 +36,7 @@ struct CompressChunk {
     int32_t ews_ctas;
     void* qb;         // tensor path: nblk x n x 64 bf16 subspace bases
     void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
+    void* aux;        // tensor path: tc_aux_bytes(nblk, nblk*ceil(b/128), m, k)
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).
@@ -46,6 +47,7 @@ struct QPlan {
     int32_t nslab;        // E - S + 1 slabs of k rows in the stacked matrix M
     int32_t kcap;         // min(kq, structural rank of M)
     int64_t slab0;        // global index of this query's first slab
+    // (pad0 below: first 128-row tile of this query's stacked matrix, tensor path)
     void* U;              // result buffers (caller device memory)
     int64_t ldu;
     void* S_out;
@@ -63,6 +65,16 @@ struct BatchHdr {
     int32_t pad;
     int64_t nslab_total;
     int64_t T;            // rows in the store when the batch was planned
+    int64_t ntiles_total; // 128-row tiles of all stacked matrices (tensor path)
+};
+
+// Grid sizes of a query launch set: the actual batch (eager launches) or the
+// executor's capacity (launches captured once into a CUDA graph and replayed).
+struct QueryGrid {
+    int nq;
+    int64_t slabs;
+    int64_t tiles;
+    int max_rows;
 };
 
 // Device pointers of a store and its query scratch, passed by value.
@@ -89,6 +101,8 @@ struct QueryArgs {
     int32_t ews_ctas;
     void* qb;         // tensor path: nq x n x 64 bf16 subspace bases
     void* ys;         // tensor path: nslab_total x k x 64 floats (Y = M Q~)
+    void* aux;        // tensor path: tc_aux_bytes(nq, aux_tiles, m, kq)
+    int64_t aux_tiles;
 };
 
 // Launch configuration chosen by the autotuner (or defaults).
@@ -113,8 +127,8 @@ inline int tc_width(int kq, int extra) {
 // launch.  `fp64` selects the double-precision instantiation (F64 store).
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu,
                             int num_sms, cudaStream_t st);
-cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, int max_rows,
-                         int flags, const Tuning& tu, int num_sms, cudaStream_t st);
+cudaError_t launch_query(const QueryArgs& a, bool fp64, const QueryGrid& g, int flags, const Tuning& tu,
+                         int num_sms, cudaStream_t st);
 struct EigPlan {
     int m = 0;          // subspace width (n for the dense path)
     bool yglob = false; // Y block in global workspace
@@ -124,10 +138,12 @@ struct EigPlan {
 EigPlan eig_plan(int n, int kq, int extra, bool fp64, bool refine);
 size_t eig_smem_bytes(int n, int m, bool fp64, bool refine, bool yglob);
 size_t eig_ws_bytes(int n, bool fp64, int ctas);
+size_t tc_aux_bytes(int64_t items, int64_t tiles, int m, int kw);
 void note_launches(int64_t n);
 void profile_enable(int on);
 void profile_reset();
 int profile_count();
 bool profile_get(int i, const char** name, int64_t* launches, double* ms);
+bool profiling_on();
 
 }  // namespace zs

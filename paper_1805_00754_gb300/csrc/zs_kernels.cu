@@ -371,12 +371,18 @@ __device__ void eig_solve(const T* __restrict__ G, int n, int m, int kw, EigWork
             T acc[MB];
 #pragma unroll
             for (int c = 0; c < MB; ++c) acc[c] = T(0);
-            for (int l = 0; l < n; ++l) {
-                const T g = G[(int64_t)l * n + i];
-                const T* qr = Q + l * ldq;
+            for (int l0 = 0; l0 < n; l0 += 8) {
+                T g[8];
 #pragma unroll
-                for (int c = 0; c < MB; ++c)
-                    if (c < m) acc[c] += g * qr[c];
+                for (int u = 0; u < 8; ++u) g[u] = (l0 + u < n) ? G[(int64_t)(l0 + u) * n + i] : T(0);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (l0 + u >= n) break;
+                    const T* qr = Q + (l0 + u) * ldq;
+#pragma unroll
+                    for (int c = 0; c < MB; ++c)
+                        if (c < m) acc[c] += g[u] * qr[c];
+                }
             }
 #pragma unroll
             for (int c = 0; c < MB; ++c)
@@ -848,15 +854,17 @@ __global__ void __launch_bounds__(256) k_ur(QueryArgs a) {
 }
 
 // Lift (Eq. 9): output rows of each slab = U_i(rows) C_slab, zero past k_q.
-template <typename T>
-__global__ void __launch_bounds__(256) k_lift(QueryArgs a, int rows_tile) {
-    extern __shared__ __align__(16) char dsm[];
-    const int k = a.k, kq = a.kq, kout = a.kout, ldk = k + 1;
-    T* Cs = (T*)dsm;                          // k x kq
-    T* Ut = Cs + (size_t)k * kq;              // rows_tile x (k+1)
-    const int tid = threadIdx.x, nt = blockDim.x;
+// A group of G lanes owns one output row; lane c of the group keeps column c
+// of C_slab in registers, reads the row of U_i (broadcast within the group)
+// and writes out[row][c] (coalesced along c).
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(256) k_lift(QueryArgs a, int grp) {
+    const int k = a.k, kq = a.kq, kout = a.kout;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = lane % grp, sub = lane / grp, rows_per_warp = 32 / grp;
     const int nq = a.hdr->nq;
     const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
+    const bool vec = (sizeof(T) == 4) && (k % 4 == 0);
     for (int64_t s = blockIdx.x; s < total; s += gridDim.x) {
         const int q = find_query(a.slab_prefix, nq, s);
         const QPlan& P = a.plans[q];
@@ -864,26 +872,54 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a, int rows_tile) {
         const BlockRange br = slab_rows(P, t, a.b, Trows);
         const T* U = (const T*)a.U + (int64_t)br.blk * a.b * k;
         const T* Cg = (const T*)a.C + s * k * kq;
+        T cc[KMAX];
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) cc[j] = (j < k && c < kq) ? Cg[j * kq + c] : T(0);
         T* out = (T*)P.U;
-        const int64_t o0 = (int64_t)br.blk * a.b + br.lo - P.ts;
-        __syncthreads();
-        for (int e = tid; e < k * kq; e += nt) Cs[e] = Cg[e];
-        for (int r0 = br.lo; r0 < br.hi; r0 += rows_tile) {
-            const int nr = min(rows_tile, br.hi - r0);
-            __syncthreads();
-            for (int e = tid; e < nr * k; e += nt) {
-                const int r = e / k, c = e - (e / k) * k;
-                Ut[r * ldk + c] = U[(int64_t)(r0 + r) * k + c];
-            }
-            __syncthreads();
-            for (int e = tid; e < nr * kout; e += nt) {
-                const int r = e / kout, c = e - (e / kout) * kout;
-                T acc = 0;
-                if (c < kq) {
-                    const T* ur = Ut + r * ldk;
-                    for (int aa = 0; aa < k; ++aa) acc += ur[aa] * Cs[aa * kq + c];
+        const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
+        // RU rows per thread per iteration, all loads issued before the math, so
+        // that enough bytes are in flight to cover HBM latency
+        constexpr int RU = 4;
+        const int step = 8 * rows_per_warp;
+        for (int r0 = br.lo + warp * rows_per_warp + sub; r0 < br.hi; r0 += RU * step) {
+            T acc[RU];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) acc[u] = T(0);
+            if (vec) {
+#pragma unroll
+                for (int j = 0; j < KMAX; j += 4) {
+                    if (j >= k) break;
+                    float4 u4[RU];
+#pragma unroll
+                    for (int u = 0; u < RU; ++u) {
+                        const int r = r0 + u * step;
+                        u4[u] = (r < br.hi) ? __ldg(reinterpret_cast<const float4*>(U + (int64_t)r * k + j))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < RU; ++u)
+                        acc[u] += (T)u4[u].x * cc[j] + (T)u4[u].y * cc[j + 1] + (T)u4[u].z * cc[j + 2] +
+                                  (T)u4[u].w * cc[j + 3];
                 }
-                out[(o0 + (r0 - br.lo) + r) * P.ldu + c] = acc;
+            } else {
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int r = r0 + u * step;
+                    if (r >= br.hi) break;
+                    const T* ur = U + (int64_t)r * k;
+#pragma unroll
+                    for (int j = 0; j < KMAX; ++j) {
+                        if (j >= k) break;
+                        acc[u] += ur[j] * cc[j];
+                    }
+                }
+            }
+            if (c < kout) {
+#pragma unroll
+                for (int u = 0; u < RU; ++u) {
+                    const int r = r0 + u * step;
+                    if (r < br.hi) out[(o0 + r) * P.ldu + c] = acc[u];
+                }
             }
         }
     }
@@ -1003,13 +1039,29 @@ static size_t tc_subspace_smem(int n, int m, bool& yglob) {
 static size_t tc_project_smem(int n, int m) {
     return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)2 * 128 * 72 * 2;
 }
-static size_t tc_rr_smem(int m, bool ref) {
-    return (size_t)4 * m * (m + 1) * (ref ? 8 : 4) + (size_t)2 * m * (m + 1) * 4;
+
+// Auxiliary scratch of the tensor path, carved from one buffer:
+// [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw]
+size_t tc_aux_bytes(int64_t items, int64_t tiles, int m, int kw) {
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    return r(4 * (size_t)tiles * m * m) + r(4 * (size_t)items * m * m) + r(4 * (size_t)items * m * kw) +
+           r(4 * (size_t)items * kw);
+}
+static void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, int kw, TcScratch& sc) {
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* p = (char*)aux;
+    sc.Hp = (float*)p;
+    p += r(4 * (size_t)tiles * m * m);
+    sc.Cq = (float*)p;
+    p += r(4 * (size_t)items * m * m);
+    sc.Zs = (float*)p;
+    p += r(4 * (size_t)items * m * kw);
+    sc.th = (float*)p;
 }
 
 template <class Src, typename Tin, bool REF, bool QUERY>
-static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int max_rows,
-                           int ews_ctas, cudaStream_t st) {
+static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
+                           int ews_ctas, int num_sms, cudaStream_t st) {
     const int ntile = (n + 127) / 128;
     const int npairs = ntile * (ntile + 1) / 2;
     const int gi = std::min(max_items, 65535);
@@ -1021,31 +1073,47 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
     {
         bool yglob;
         const size_t sm = tc_subspace_smem(n, sc.m, yglob);
-        ZS_TRY(set_smem(k_subspace<Src>, sm));
+        const int gs = std::min(gi, yglob ? ews_ctas : 65535);
         prof::Scope ps(QUERY ? "subspace_query" : "subspace", st);
-        k_subspace<Src><<<std::min(gi, yglob ? ews_ctas : 65535), 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+        if (sc.m <= 32) {
+            ZS_TRY(set_smem(k_subspace<Src, 32>, sm));
+            k_subspace<Src, 32><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+        } else {
+            ZS_TRY(set_smem(k_subspace<Src, 64>, sm));
+            k_subspace<Src, 64><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+        }
     }
     ZS_TRY(cudaGetLastError());
     {
         const size_t sm = tc_project_smem(n, sc.m);
         ZS_TRY(set_smem(k_project<Src, Tin>, sm));
         prof::Scope ps(QUERY ? "project_query" : "project", st);
-        k_project<Src, Tin><<<dim3((max_rows + 127) / 128, gi), 256, sm, st>>>(src, sc, n);
+        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * 8);
+        k_project<Src, Tin><<<std::max(gp, 1), 256, sm, st>>>(src, sc, n);
     }
     ZS_TRY(cudaGetLastError());
     {
-        const size_t sm = tc_rr_smem(sc.m, REF);
-        ZS_TRY(set_smem(k_rr<Src, REF, QUERY>, sm));
-        prof::Scope ps(QUERY ? "rr_query" : "rr", st);
-        k_rr<Src, REF, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
+        const size_t per = rr_warp_bytes<REF>(sc.m);
+        const int wpc = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / per));
+        const size_t sm = per * wpc;
+        ZS_TRY(set_smem(k_rr_core<Src, REF>, sm));
+        prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
+        k_rr_core<Src, REF><<<std::min((max_items + wpc - 1) / wpc, 65535), 32 * wpc, sm, st>>>(src, sc, kw);
     }
     ZS_TRY(cudaGetLastError());
-    note_launches(4);
+    {
+        const size_t sm = sizeof(float) * ((size_t)sc.m * kw + (size_t)n * kw);
+        ZS_TRY(set_smem(k_rr_out<Src, QUERY>, sm));
+        prof::Scope ps(QUERY ? "rr_out_query" : "rr_out", st);
+        k_rr_out<Src, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
+    }
+    ZS_TRY(cudaGetLastError());
+    note_launches(5);
     return cudaSuccess;
 }
 
 template <typename Tin, bool REF>
-static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, cudaStream_t st) {
+static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num_sms, cudaStream_t st) {
     TcScratch sc;
     sc.G = (float*)c.G;
     sc.Qb = (__nv_bfloat16*)c.qb;
@@ -1054,8 +1122,10 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, cudaStr
     sc.ews_ctas = std::max(1, c.ews_ctas);
     sc.m = tc_width(c.k, tu.eig_m_extra);
     sc.power_its = tu.power_its;
+    tc_aux_carve(c.aux, c.nblk, (int64_t)c.nblk * ((c.b + 127) / 128), sc.m, c.k, sc);
     SrcCompress src{c};
-    return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk, c.b, sc.ews_ctas, st);
+    return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,
+                                                 (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms, st);
 }
 
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
@@ -1063,8 +1133,9 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
     const bool ref = (flags & 1) != 0;
     if (use_tc_path(fp64, c.n, flags)) {
         if (c.in_kind == IN_BF16)
-            return ref ? compress_tc<__nv_bfloat16, true>(c, tu, st) : compress_tc<__nv_bfloat16, false>(c, tu, st);
-        return ref ? compress_tc<float, true>(c, tu, st) : compress_tc<float, false>(c, tu, st);
+            return ref ? compress_tc<__nv_bfloat16, true>(c, tu, num_sms, st)
+                       : compress_tc<__nv_bfloat16, false>(c, tu, num_sms, st);
+        return ref ? compress_tc<float, true>(c, tu, num_sms, st) : compress_tc<float, false>(c, tu, num_sms, st);
     }
     if (fp64) return compress_impl<double, double, false>(c, tu, num_sms, st);
     if (c.in_kind == IN_BF16)
@@ -1074,9 +1145,24 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
                : compress_impl<float, float, false>(c, tu, num_sms, st);
 }
 
+template <typename T>
+static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int pers, cudaStream_t st) {
+    int grp = 1;
+    while (grp < a.kout) grp <<= 1;               // lanes per output row
+    if (grp > 32) return cudaErrorInvalidValue;
+    prof::Scope ps("lift", st);
+    const int grid = (int)std::min<int64_t>(max_slabs, pers);
+    if (a.k <= 16) k_lift<T, 16><<<grid, 256, 0, st>>>(a, grp);
+    else if (a.k <= 32) k_lift<T, 32><<<grid, 256, 0, st>>>(a, grp);
+    else k_lift<T, 64><<<grid, 256, 0, st>>>(a, grp);
+    return cudaGetLastError();
+}
+
 template <typename T, bool REF>
-static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs, int max_rows, int flags,
-                              const Tuning& tu, int num_sms, cudaStream_t st) {
+static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu, int num_sms,
+                              cudaStream_t st) {
+    const int max_nq = g.nq;
+    const int64_t max_slabs = g.slabs;
     const bool fp64 = std::is_same<T, double>::value;
     const int k = a.k, n = a.n, kq = a.kq;
     const int pers = std::max(1, num_sms * tu.slab_ctas_per_sm);
@@ -1107,8 +1193,9 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
             sc.ews_ctas = std::max(1, a.ews_ctas);
             sc.m = tc_width(kq, tu.eig_m_extra);
             sc.power_its = tu.power_its;
+            tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
             SrcQuery src{a};
-            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, max_rows, sc.ews_ctas, st)));
+            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms, st)));
             {
                 const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
                 ZS_TRY(set_smem(k_bfix, sm));
@@ -1117,12 +1204,7 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
                 ZS_TRY(cudaGetLastError());
             }
             {
-                const int rt = tu.lift_rows;
-                const size_t sm = sizeof(T) * ((size_t)k * kq + (size_t)rt * (k + 1)) + 64;
-                ZS_TRY(set_smem(k_lift<T>, sm));
-                prof::Scope ps("lift", st);
-                k_lift<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, sm, st>>>(a, rt);
-                ZS_TRY(cudaGetLastError());
+                ZS_TRY(launch_lift<T>(a, max_slabs, pers, st));
             }
             note_launches(4);
             return cudaSuccess;
@@ -1158,23 +1240,18 @@ static cudaError_t query_impl(const QueryArgs& a, int max_nq, int64_t max_slabs,
         k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
-    {
-        const int rt = tu.lift_rows;
-        const size_t sm = sizeof(T) * ((size_t)k * kq + (size_t)rt * (k + 1)) + 64;
-        ZS_TRY(set_smem(k_lift<T>, sm));
-        prof::Scope ps("lift", st);
-        k_lift<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, sm, st>>>(a, rt);
-        ZS_TRY(cudaGetLastError());
-    }
+    ZS_TRY(launch_lift<T>(a, max_slabs, pers, st));
     note_launches(6);
     return cudaSuccess;
 }
 
-cudaError_t launch_query(const QueryArgs& a, bool fp64, int max_nq, int64_t max_slabs, int max_rows, int flags,
-                         const Tuning& tu, int num_sms, cudaStream_t st) {
-    if (fp64) return query_impl<double, false>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st);
-    return a.fp64_refine ? query_impl<float, true>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st)
-                         : query_impl<float, false>(a, max_nq, max_slabs, max_rows, flags, tu, num_sms, st);
+cudaError_t launch_query(const QueryArgs& a, bool fp64, const QueryGrid& g, int flags, const Tuning& tu,
+                         int num_sms, cudaStream_t st) {
+    if (fp64) return query_impl<double, false>(a, g, flags, tu, num_sms, st);
+    return a.fp64_refine ? query_impl<float, true>(a, g, flags, tu, num_sms, st)
+                         : query_impl<float, false>(a, g, flags, tu, num_sms, st);
 }
+
+bool profiling_on() { return prof::g_on.load() != 0; }
 
 }  // namespace zs

@@ -92,8 +92,13 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
     __syncthreads();
     if (m < 2) return 0;
     const int mm = m + (m & 1), np = mm >> 1;
-    const T tol = T(2) * eps_of<T>();
-    const T floor_ = eps_of<T>() * js.scale;
+    // a pair counts as converged once |a_pq| <= 64 eps sqrt(a_pp a_qq): the
+    // rounding noise of the parallel updates sits near eps |A|, so a tighter
+    // threshold only burns sweeps; the eigenvalue error left is O(tol^2).
+    const T tol = T(64) * eps_of<T>();
+    // absolute floor: in FP32 the updates leave noise ~eps * max|a_ii| in every
+    // entry, so pairs between small eigenvalues would otherwise rotate forever
+    const T floor_ = (sizeof(T) == 4 ? T(64) : T(1)) * eps_of<T>() * js.scale;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) js.flag = 0;
@@ -217,6 +222,99 @@ __device__ void mgs_orth(T* Q, int ldq, int n, int m, T* red, T* coef) {
         for (int i = tid; i < n; i += nt) Q[i * ldq + c] *= inv;
         __syncthreads();
     }
+}
+
+
+// ---------------------------------------------------------------------------
+// Warp-level variants: one warp owns one small problem in its own shared
+// memory slice and synchronises with __syncwarp only, so the warps of a CTA
+// work on different problems without CTA barriers.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ int warp_jacobi(T* A, int lda, T* Z, int ldz, int m, int max_sweeps, bool init_z) {
+    const int lane = threadIdx.x & 31;
+    if (init_z)
+        for (int e = lane; e < m * m; e += 32) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
+    __syncwarp();
+    if (m < 2) return 0;
+    T mx = 0;
+    for (int i = lane; i < m; i += 32) mx = fmax(mx, zabs(A[i * lda + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int mm = m + (m & 1), np = mm >> 1;
+    const T tol = T(64) * eps_of<T>();
+    const T floor_ = (sizeof(T) == 4 ? T(64) : T(1)) * eps_of<T>() * mx;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int r = 0; r < mm - 1; ++r) {
+            // pair of this lane (np <= 32 pairs for m <= 64)
+            int p = 0, q = 0;
+            T c = 1, s = 0;
+            if (lane < np) {
+                rr_pair(mm, r, lane, p, q);
+                if (q < m) {
+                    const T apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
+                    const T aa = zabs(apq);
+                    if (aa > floor_ && aa > tol * zsqrt(zabs(app * aqq))) {
+                        const T tau = (aqq - app) / (T(2) * apq);
+                        const T t = (tau >= T(0) ? T(1) : T(-1)) / (zabs(tau) + zsqrt(T(1) + tau * tau));
+                        c = T(1) / zsqrt(T(1) + t * t);
+                        s = t * c;
+                    }
+                }
+            }
+            rotated |= __any_sync(0xffffffffu, s != T(0));
+            __syncwarp();
+            // rows: A <- J^T A ; pair i handled via shuffles of (p, q, c, s)
+            for (int i = 0; i < np; ++i) {
+                const T si = __shfl_sync(0xffffffffu, s, i);
+                if (si == T(0)) continue;
+                const T ci = __shfl_sync(0xffffffffu, c, i);
+                const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
+                for (int j = lane; j < m; j += 32) {
+                    const T ap = A[pi * lda + j], aq = A[qi * lda + j];
+                    A[pi * lda + j] = ci * ap - si * aq;
+                    A[qi * lda + j] = si * ap + ci * aq;
+                }
+            }
+            __syncwarp();
+            // columns: A <- A J, Z <- Z J
+            for (int i = 0; i < np; ++i) {
+                const T si = __shfl_sync(0xffffffffu, s, i);
+                if (si == T(0)) continue;
+                const T ci = __shfl_sync(0xffffffffu, c, i);
+                const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
+                for (int row = lane; row < m; row += 32) {
+                    const T ap = A[row * lda + pi], aq = A[row * lda + qi];
+                    A[row * lda + pi] = ci * ap - si * aq;
+                    A[row * lda + qi] = si * ap + ci * aq;
+                    const T zp = Z[row * ldz + pi], zq = Z[row * ldz + qi];
+                    Z[row * ldz + pi] = ci * zp - si * zq;
+                    Z[row * ldz + qi] = si * zp + ci * zq;
+                }
+            }
+            __syncwarp();
+        }
+        if (!rotated) break;
+    }
+    return sweep;
+}
+
+// perm[r] = index of the r-th largest diagonal entry (warp-level, stable).
+template <typename T>
+__device__ void warp_sort_desc(const T* A, int lda, int m, int* perm) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < m; i += 32) {
+        const T v = A[i * lda + i];
+        int rk = 0;
+        for (int j = 0; j < m; ++j) {
+            const T w = A[j * lda + j];
+            rk += (w > v) || (w == v && j < i);
+        }
+        perm[rk] = i;
+    }
+    __syncwarp();
 }
 
 }  // namespace zs

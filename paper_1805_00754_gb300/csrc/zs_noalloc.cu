@@ -91,8 +91,12 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         while (ews_ctas > 1 && zs::eig_ws_bytes((int)n, fp64, ews_ctas) > kNoAllocScratchBytes / 4) ews_ctas /= 2;
         ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
     }
-    const size_t qper = ((2 * mt * (size_t)n) + 255) & ~(size_t)255;
-    const size_t yper = ((4 * mt * (size_t)b) + 255) & ~(size_t)255;
+    auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t qper = r256(2 * mt * (size_t)n);
+    const size_t proj = r256(4 * mt * (size_t)b);
+    // Rayleigh-Ritz scratch of one block (tile partials, Q~^T Q~, Ritz data) with slack for alignment
+    const size_t auxp = tc ? r256(4 * mt * mt * ((b + 127) / 128 + 1) + 4 * mt * k + 4 * k + 1024) : 0;
+    const size_t yper = proj + auxp;
     const size_t gper = ((ts * (size_t)n * n) + 255) & ~(size_t)255;
     if (ews_bytes + gper + qper + yper > kNoAllocScratchBytes)
         return zs::fail(ZS_EINVAL, "n=%lld needs %zu scratch bytes per block; the no-alloc scratch holds %zu",
@@ -116,6 +120,8 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         ch.G = (char*)scratch + ews_bytes;
         ch.qb = tc ? (char*)scratch + ews_bytes + gper * chunk : nullptr;
         ch.ys = tc ? (char*)scratch + ews_bytes + (gper + qper) * chunk : nullptr;
+        // the Rayleigh-Ritz scratch follows the projections of the chunk
+        ch.aux = tc ? (char*)ch.ys + proj * chunk : nullptr;
         ch.ews = (ep.yglob || tc) ? scratch : nullptr;
         ch.ews_ctas = ews_ctas;
         ch.U = (char*)U + ts * (size_t)j0 * b * k;

@@ -46,6 +46,13 @@ struct SrcCompress {
         return (const char*)c.A + (size_t)j * c.b * c.lda * elem;
     }
     __device__ __forceinline__ int64_t ybase(int j) const { return (int64_t)j * c.b; }   // Y row offset
+    __device__ __forceinline__ int64_t tile0(int j) const { return (int64_t)j * ((c.b + 127) / 128); }
+    __device__ __forceinline__ int64_t ntiles() const { return (int64_t)c.nblk * ((c.b + 127) / 128); }
+    __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
+        const int tpi = (c.b + 127) / 128;
+        item = (int)(t / tpi);
+        rt = (int)(t - (int64_t)item * tpi);
+    }
 };
 
 struct SrcQuery {
@@ -57,6 +64,17 @@ struct SrcQuery {
         return (const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem;
     }
     __device__ __forceinline__ int64_t ybase(int q) const { return a.plans[q].slab0 * a.k; }
+    __device__ __forceinline__ int64_t tile0(int q) const { return a.plans[q].pad0; }
+    __device__ __forceinline__ int64_t ntiles() const { return a.hdr->ntiles_total; }
+    __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
+        int lo = 0, hi = a.hdr->nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.plans[mid].pad0 <= t) lo = mid; else hi = mid - 1;
+        }
+        item = lo;
+        rt = (int)(t - a.plans[lo].pad0);
+    }
 };
 
 // Scratch for the tensor path (per launch).
@@ -68,6 +86,10 @@ struct TcScratch {
     int ews_ctas;
     int m;                  // subspace width (multiple of 8, <= 64)
     int power_its;          // power steps on G~
+    float* Hp;              // per 128-row tile of Y: Y_t^T Y_t (m x m)
+    float* Cq;              // items x m x m: Q~^T Q~
+    float* Zs;              // items x m x kw: Ritz coefficients
+    float* th;              // items x kw: Ritz values (sigma^2)
 };
 
 template <typename Tin>
@@ -183,7 +205,7 @@ __global__ void __launch_bounds__(256, 2) k_gram_lo(Src src, TcScratch sc, int n
 // 2. Dominant m-dimensional subspace of G~ (rough): pivoted columns, then
 //    power steps, each followed by Gram-Schmidt; stored as bf16 (n x m).
 // ---------------------------------------------------------------------------
-template <class Src>
+template <class Src, int MB>
 __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, int yglob) {
     extern __shared__ __align__(16) char dsm[];
     __shared__ int piv[ZS_MAXM];
@@ -216,18 +238,24 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
         mgs_orth<float>(Q, ldq, n, m, red, coef);
         for (int it = 0; it < sc.power_its; ++it) {
             for (int i = tid; i < n; i += nt) {
-                float acc[ZS_MAXM];
+                float acc[MB];
 #pragma unroll
-                for (int c = 0; c < ZS_MAXM; ++c) acc[c] = 0.f;
-                for (int l = 0; l < n; ++l) {
-                    const float g = G[(size_t)l * n + i];
-                    const float* qr = Q + l * ldq;
+                for (int c = 0; c < MB; ++c) acc[c] = 0.f;
+                for (int l0 = 0; l0 < n; l0 += 8) {
+                    float g[8];
 #pragma unroll
-                    for (int c = 0; c < ZS_MAXM; ++c)
-                        if (c < m) acc[c] += g * qr[c];
+                    for (int u = 0; u < 8; ++u) g[u] = (l0 + u < n) ? __ldg(G + (size_t)(l0 + u) * n + i) : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        if (l0 + u >= n) break;
+                        const float* qr = Q + (l0 + u) * ldq;
+#pragma unroll
+                        for (int c = 0; c < MB; ++c)
+                            if (c < m) acc[c] += g[u] * qr[c];
+                    }
                 }
 #pragma unroll
-                for (int c = 0; c < ZS_MAXM; ++c)
+                for (int c = 0; c < MB; ++c)
                     if (c < m) Y[i * ldq + c] = acc[c];
             }
             __syncthreads();
@@ -239,9 +267,23 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
             mgs_orth<float>(Q, ldq, n, m, red, coef);
         }
         __nv_bfloat16* Qb = sc.Qb + (size_t)item * n * m;
+        __syncthreads();
         for (int e = tid; e < n * m; e += nt) {
             const int i = e / m, c = e - (e / m) * m;
-            Qb[e] = __float2bfloat16_rn(Q[i * ldq + c]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(Q[i * ldq + c]);
+            Qb[e] = h;
+            Q[i * ldq + c] = __bfloat162float(h);       // Q~ as it will be used
+        }
+        __syncthreads();
+        // C = Q~^T Q~ (exact products of bf16 values, fp32 sums)
+        float* Cq = sc.Cq + (size_t)item * m * m;
+        for (int e = tid; e < m * m; e += nt) {
+            const int a = e / m, c = e - (e / m) * m;
+            if (c < a) continue;
+            float acc = 0.f;
+            for (int i = 0; i < n; ++i) acc += Q[i * ldq + a] * Q[i * ldq + c];
+            Cq[a * m + c] = acc;
+            Cq[c * m + a] = acc;
         }
     }
 }
@@ -261,9 +303,12 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
     const int64_t ld = src.ld();
     const int ntn = m / 8;
     int loaded = -1;
-    for (int item = blockIdx.y; item < src.count(); item += gridDim.y) {
+    const int64_t ntiles = src.ntiles();
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int item, rt;
+        src.tile_item(tile, item, rt);
         const int rows = src.rows(item);
-        const int r0 = blockIdx.x * 128;
+        const int r0 = rt * 128;
         if (r0 >= rows) continue;
         const Tin* X = (const Tin*)src.X(item, sizeof(Tin));
         __syncthreads();
@@ -326,196 +371,219 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
             }
         }
         float* Y = sc.Y + (size_t)src.ybase(item) * m;
+        __syncthreads();
+        float* Ys = reinterpret_cast<float*>(Xh);      // 128 x (m+1), reuses the X staging
+        const int ldy = m + 1;
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             if (nt >= ntn) break;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int r = r0 + warp * 16 + (lane >> 2) + ((e >> 1) ? 8 : 0);
+                const int rl = warp * 16 + (lane >> 2) + ((e >> 1) ? 8 : 0);
                 const int c = nt * 8 + 2 * (lane & 3) + (e & 1);
+                const int r = r0 + rl;
                 if (r < rows) Y[(size_t)r * m + c] = acc[nt][e];
+                Ys[rl * ldy + c] = (r < rows) ? acc[nt][e] : 0.f;
             }
+        }
+        __syncthreads();
+        // this tile's share of Y^T Y (fixed summation order -> deterministic)
+        float* Hp = sc.Hp + (size_t)tile * m * m;
+        const int nr = min(128, rows - r0);
+        for (int e = tid; e < m * m; e += 256) {
+            const int a = e / m, c = e - (e / m) * m;
+            if (c < a) continue;
+            float h = 0.f;
+            for (int r = 0; r < nr; ++r) h += Ys[r * ldy + a] * Ys[r * ldy + c];
+            Hp[a * m + c] = h;
+            Hp[c * m + a] = h;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 4. Rayleigh-Ritz on span(Q~) and the outputs.
+// 4a. Rayleigh-Ritz core, one warp per item: H = sum of the tiles' Y^T Y,
+//     C = Q~^T Q~ = L L^T, H' = L^-1 H L^-T, Jacobi H' = W Theta W^T
+//     (FP32 sweeps; with REF one FP64 refinement on W^T H' W), Z = L^-T W.
 // ---------------------------------------------------------------------------
-template <typename TR>
-__device__ void sym_pairs_accumulate(const float* __restrict__ A, int64_t lda, const __nv_bfloat16* __restrict__ Ab,
-                                     int rows, int m, float* st, TR* out, int ldo) {
-    // out[a][c] = sum_r A[r][a] A[r][c]  (upper triangle computed, mirrored)
-    const int tid = threadIdx.x, nt = blockDim.x, lds = m + 1;
-    constexpr int NS = (ZS_MAXM * (ZS_MAXM + 1) / 2 + 255) / 256;
-    const int np = m * (m + 1) / 2;
-    TR acc[NS];
-    int pa[NS], pc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        acc[s] = 0;
-        int e = tid + s * nt, aa = 0;
-        while (aa < m && e >= m - aa) { e -= m - aa; ++aa; }
-        pa[s] = aa;
-        pc[s] = aa + e;
-    }
-    for (int r0 = 0; r0 < rows; r0 += 32) {
-        const int nr = min(32, rows - r0);
-        __syncthreads();
-        for (int e = tid; e < nr * m; e += nt) {
-            const int r = e / m, c = e - (e / m) * m;
-            st[r * lds + c] = A ? A[(int64_t)(r0 + r) * lda + c] : __bfloat162float(Ab[(int64_t)(r0 + r) * lda + c]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            if (tid + s * nt < np) {
-                TR t = 0;
-                for (int r = 0; r < nr; ++r) t += (TR)st[r * lds + pa[s]] * (TR)st[r * lds + pc[s]];
-                acc[s] += t;
-            }
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-        if (tid + s * nt < np) {
-            out[pa[s] * ldo + pc[s]] = acc[s];
-            out[pc[s] * ldo + pa[s]] = acc[s];
-        }
-    __syncthreads();
+template <bool REF>
+__host__ __device__ __forceinline__ size_t rr_warp_bytes(int m) {
+    const size_t ld = m + 1;
+    const size_t tr = REF ? 8 : 4;
+    // Hs, Cs(L), Li in TR; A_T, Z_T in float; REF: X, W in double
+    size_t b = 3 * tr * m * ld + 2 * 4 * m * ld + (REF ? 2 * 8 * m * ld : 0) + 4 * 64 + 8 * 64;
+    return (b + 15) & ~size_t(15);
 }
 
-template <class Src, bool REF, bool QUERY>
-__global__ void __launch_bounds__(256) k_rr(Src src, TcScratch sc, int n, int kw) {
+template <class Src, bool REF>
+__global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) {
     using TR = typename std::conditional<REF, double, float>::type;
     extern __shared__ __align__(16) char dsm[];
-    __shared__ JacobiScratch<float> js;
-    __shared__ JacobiScratch<double> jd;
-    __shared__ int perm[ZS_MAXM];
-    __shared__ TR theta[ZS_MAXM];
-    __shared__ float sig[ZS_MAXM];
-    __shared__ int sgn[ZS_MAXM];
-    __shared__ int s_rank;
     const int m = sc.m, ld = m + 1;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    TR* Hb = (TR*)dsm;                     // H, then H'
-    TR* Cb = Hb + (size_t)m * ld;          // C, then L, then W (REF)
-    TR* Li = Cb + (size_t)m * ld;          // L^{-1}, then Z
-    TR* Tb = Li + (size_t)m * ld;          // temp, then X (REF)
-    float* A_T = (float*)(Tb + (size_t)m * ld);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    char* base = dsm + (size_t)warp * rr_warp_bytes<REF>(m);
+    TR* Hs = (TR*)base;
+    TR* Cs = Hs + (size_t)m * ld;
+    TR* Li = Cs + (size_t)m * ld;
+    float* A_T = (float*)(Li + (size_t)m * ld);
     float* Z_T = A_T + (size_t)m * ld;
-    float* stg = A_T;                      // staging aliases the Jacobi buffers
+    double* X = (double*)(Z_T + (size_t)m * ld + ((m * ld) & 1));
+    double* W = X + (REF ? (size_t)m * ld : 0);
+    int* perm = (int*)(base + rr_warp_bytes<REF>(m) - 4 * 64 - 8 * 64);
+    double* thd = (double*)(base + rr_warp_bytes<REF>(m) - 8 * 64);
+    const int count = src.count();
+    for (int item = blockIdx.x * wpc + warp; item < count; item += gridDim.x * wpc) {
+        const int rows = src.rows(item);
+        const int ntiles = (rows + 127) / 128;
+        const float* Hp = sc.Hp + (size_t)src.tile0(item) * m * m;
+        const float* Cq = sc.Cq + (size_t)item * m * m;
+        for (int e = lane; e < m * m; e += 32) {
+            TR h = 0;
+            for (int t = 0; t < ntiles; ++t) h += (TR)Hp[(size_t)t * m * m + e];
+            Hs[(e / m) * ld + e % m] = h;
+            Cs[(e / m) * ld + e % m] = (TR)Cq[e];
+        }
+        __syncwarp();
+        // Cholesky C = L L^T (lower, in place)
+        for (int j = 0; j < m; ++j) {
+            if (lane == 0) {
+                TR d = Cs[j * ld + j];
+                for (int p = 0; p < j; ++p) d -= Cs[j * ld + p] * Cs[j * ld + p];
+                Cs[j * ld + j] = d > TR(1e-12) ? (TR)sqrt((double)d) : TR(1e-6);
+            }
+            __syncwarp();
+            for (int i = j + 1 + lane; i < m; i += 32) {
+                TR d = Cs[i * ld + j];
+                for (int p = 0; p < j; ++p) d -= Cs[i * ld + p] * Cs[j * ld + p];
+                Cs[i * ld + j] = d / Cs[j * ld + j];
+            }
+            __syncwarp();
+        }
+        for (int c = lane; c < m; c += 32)
+            for (int i = 0; i < m; ++i) {
+                if (i < c) { Li[i * ld + c] = 0; continue; }
+                TR d = (i == c) ? TR(1) : TR(0);
+                for (int p = c; p < i; ++p) d -= Cs[i * ld + p] * Li[p * ld + c];
+                Li[i * ld + c] = d / Cs[i * ld + i];
+            }
+        __syncwarp();
+        // H' = L^-1 H L^-T  (temp in Cs, L no longer needed)
+        for (int e = lane; e < m * m; e += 32) {
+            const int i = e / m, c = e % m;
+            TR d = 0;
+            for (int p = 0; p <= i; ++p) d += Li[i * ld + p] * Hs[p * ld + c];
+            Cs[i * ld + c] = d;
+        }
+        __syncwarp();
+        for (int e = lane; e < m * m; e += 32) {
+            const int i = e / m, c = e % m;
+            TR d = 0;
+            for (int p = 0; p <= c; ++p) d += Cs[i * ld + p] * Li[c * ld + p];
+            Hs[i * ld + c] = d;
+        }
+        __syncwarp();
+        for (int e = lane; e < m * m; e += 32) {
+            const int i = e / m, c = e % m;
+            const TR v = (Hs[i * ld + c] + Hs[c * ld + i]) * TR(0.5);
+            A_T[i * ld + c] = (float)v;
+            if (REF) X[i * ld + c] = (double)v;
+        }
+        __syncwarp();
+        warp_jacobi<float>(A_T, ld, Z_T, ld, m, 30, true);
+        const double* Zsrc_d = nullptr;
+        if constexpr (REF) {
+            // B = Z^T H' Z in FP64 (X holds H'), then FP64 Jacobi (refinement)
+            double* Hd = (double*)Hs;                    // reuse: Hs is double when REF
+            for (int e = lane; e < m * m; e += 32) {
+                const int i = e / m, c = e % m;
+                double d = 0;
+                for (int l = 0; l < m; ++l) d += X[i * ld + l] * (double)Z_T[l * ld + c];
+                Hd[i * ld + c] = d;                       // H' Z
+            }
+            __syncwarp();
+            for (int e = lane; e < m * m; e += 32) {
+                const int a = e / m, c = e % m;
+                double d = 0;
+                for (int i = 0; i < m; ++i) d += (double)Z_T[i * ld + a] * Hd[i * ld + c];
+                X[a * ld + c] = d;                        // B
+            }
+            __syncwarp();
+            warp_jacobi<double>(X, ld, W, ld, m, 4, true);
+            for (int e = lane; e < m * m; e += 32) {
+                const int i = e / m, c = e % m;
+                double d = 0;
+                for (int a = 0; a < m; ++a) d += (double)Z_T[i * ld + a] * W[a * ld + c];
+                Hd[i * ld + c] = d;                       // Z W
+            }
+            __syncwarp();
+            warp_sort_desc<double>(X, ld, m, perm);
+            for (int c = lane; c < m; c += 32) thd[c] = X[perm[c] * ld + perm[c]];
+            Zsrc_d = Hd;
+        } else {
+            warp_sort_desc<float>(A_T, ld, m, perm);
+            for (int c = lane; c < m; c += 32) thd[c] = (double)A_T[perm[c] * ld + perm[c]];
+        }
+        __syncwarp();
+        // Z = L^-T W(:, perm) for the kw wanted pairs
+        float* Zg = sc.Zs + (size_t)item * m * kw;
+        for (int e = lane; e < m * kw; e += 32) {
+            const int a = e / kw, c = e % kw;
+            const int pc = perm[c];
+            double d = 0;
+            for (int p = a; p < m; ++p)
+                d += (double)Li[p * ld + a] * (REF ? Zsrc_d[p * ld + pc] : (double)Z_T[p * ld + pc]);
+            Zg[e] = (float)d;
+        }
+        for (int c = lane; c < kw; c += 32) sc.th[(size_t)item * kw + c] = (float)thd[c];
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 4b. Outputs per item: sigma = sqrt(theta), V = Q~ Z (signed), U = Y Z Sigma^-1.
+// ---------------------------------------------------------------------------
+template <class Src, bool QUERY>
+__global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, int kw) {
+    extern __shared__ __align__(16) char dsm[];
+    const int m = sc.m;
+    float* Zsm = (float*)dsm;                  // m x kw
+    float* Vs = Zsm + (size_t)m * kw;          // n x kw
+    __shared__ float sig[ZS_MAXM];
+    __shared__ float sgnf[ZS_MAXM];
+    __shared__ int s_rank;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     for (int item = blockIdx.x; item < src.count(); item += gridDim.x) {
         const int rows = src.rows(item);
         const float* Y = sc.Y + (size_t)src.ybase(item) * m;
         const __nv_bfloat16* Qb = sc.Qb + (size_t)item * n * m;
-        sym_pairs_accumulate<TR>(Y, m, nullptr, rows, m, stg, Hb, ld);
-        sym_pairs_accumulate<TR>(nullptr, m, Qb, n, m, stg, Cb, ld);
-        // Cholesky C = L L^T in place (lower)
-        for (int j = 0; j < m; ++j) {
-            if (tid == 0) {
-                TR d = Cb[j * ld + j];
-                for (int p = 0; p < j; ++p) d -= Cb[j * ld + p] * Cb[j * ld + p];
-                Cb[j * ld + j] = d > TR(1e-12) ? (TR)sqrt((double)d) : TR(1e-6);
-            }
-            __syncthreads();
-            for (int i = j + 1 + tid; i < m; i += nt) {
-                TR d = Cb[i * ld + j];
-                for (int p = 0; p < j; ++p) d -= Cb[i * ld + p] * Cb[j * ld + p];
-                Cb[i * ld + j] = d / Cb[j * ld + j];
-            }
-            __syncthreads();
-        }
-        // L^{-1} by forward substitution, one column per thread
-        for (int c = tid; c < m; c += nt) {
-            for (int i = 0; i < m; ++i) {
-                if (i < c) { Li[i * ld + c] = 0; continue; }
-                TR d = (i == c) ? TR(1) : TR(0);
-                for (int p = c; p < i; ++p) d -= Cb[i * ld + p] * Li[p * ld + c];
-                Li[i * ld + c] = d / Cb[i * ld + i];
-            }
-        }
         __syncthreads();
-        // H' = L^{-1} H L^{-T}
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = e / m, c = e - (e / m) * m;
-            TR d = 0;
-            for (int p = 0; p <= i; ++p) d += Li[i * ld + p] * Hb[p * ld + c];
-            Tb[i * ld + c] = d;
-        }
-        __syncthreads();
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = e / m, c = e - (e / m) * m;
-            TR d = 0;
-            for (int p = 0; p <= c; ++p) d += Tb[i * ld + p] * Li[c * ld + p];
-            Hb[i * ld + c] = d;
-        }
-        __syncthreads();
-        for (int e = tid; e < m * m; e += nt) {
-            const int i = e / m, c = e - (e / m) * m;
-            const TR v = (Hb[i * ld + c] + Hb[c * ld + i]) * TR(0.5);
-            A_T[i * ld + c] = (float)v;
-        }
-        __syncthreads();
-        if constexpr (REF) {
-            for (int e = tid; e < m * m; e += nt) {
-                const int i = e / m, c = e - (e / m) * m;
-                Tb[i * ld + c] = (Hb[i * ld + c] + Hb[c * ld + i]) * 0.5;
-            }
-            __syncthreads();
-            for (int e = tid; e < m * m; e += nt) Hb[(e / m) * ld + e % m] = Tb[(e / m) * ld + e % m];
-            __syncthreads();
-        }
-        // small core: FP32 Jacobi, then (REF) one FP64 refinement on Z^T H' Z
-        SmallEig<float, REF> se;
-        se.A_T = A_T;
-        se.Z_T = Z_T;
-        se.A_R = REF ? (double*)Hb : nullptr;
-        se.X = REF ? (double*)Tb : nullptr;
-        se.W = REF ? (double*)Cb : nullptr;
-        se.ld = ld;
-        TR* Zo;
-        small_eig<float, REF>(se, m, js, jd, theta, perm, Zo);
-        // Z = L^{-T} W(:, perm) for the kw wanted pairs -> Li (its own rows free as we go? use Tb/Hb)
-        TR* Zc = REF ? (TR*)Hb : Tb;           // m x kw (ld)
-        if (REF) {
-            // Hb held A_R (consumed); Zo = X = Tb
-            for (int e = tid; e < m * kw; e += nt) {
-                const int a = e / kw, c = e - (e / kw) * kw;
-                TR d = 0;
-                for (int p = a; p < m; ++p) d += Li[p * ld + a] * Zo[p * ld + perm[c]];
-                Zc[a * ld + c] = d;
-            }
-        } else {
-            for (int e = tid; e < m * kw; e += nt) {
-                const int a = e / kw, c = e - (e / kw) * kw;
-                TR d = 0;
-                for (int p = a; p < m; ++p) d += Li[p * ld + a] * (TR)Zo[p * ld + perm[c]];
-                Zc[a * ld + c] = d;
-            }
-        }
-        __syncthreads();
-        int kcap = kw;
+        for (int e = tid; e < m * kw; e += nt) Zsm[e] = sc.Zs[(size_t)item * m * kw + e];
+        int kcap;
         if constexpr (QUERY) kcap = src.a.plans[item].kcap;
         else kcap = min(kw, min(rows, n));
         if (tid == 0) s_rank = 0;
         __syncthreads();
-        const float s0 = sqrtf(fmaxf((float)theta[0], 0.f));
+        const float s0 = sqrtf(fmaxf(sc.th[(size_t)item * kw], 0.f));
         for (int c = tid; c < kw; c += nt) {
-            float s = sqrtf(fmaxf((float)theta[c], 0.f));
-            if (!(c < kcap && s > kRankTolF32 * s0)) s = 0.f;
-            sig[c] = s;
-            if (s > 0.f) atomicAdd(&s_rank, 1);
+            float sv = sqrtf(fmaxf(sc.th[(size_t)item * kw + c], 0.f));
+            if (!(c < kcap && sv > kRankTolF32 * s0)) sv = 0.f;
+            sig[c] = sv;
+            if (sv > 0.f) atomicAdd(&s_rank, 1);
         }
-        // sign: largest-|.| entry of v_c = Q~ z_c positive (lowest index on ties)
+        // V = Q~ Z
+        for (int e = tid; e < n * kw; e += nt) {
+            const int l = e / kw, c = e - (e / kw) * kw;
+            float v = 0.f;
+            const __nv_bfloat16* qr = Qb + (size_t)l * m;
+            for (int a = 0; a < m; ++a) v += __bfloat162float(qr[a]) * Zsm[a * kw + c];
+            Vs[e] = v;
+        }
+        __syncthreads();
         for (int c = wid; c < kw; c += nw) {
             float best = -1.f;
             int bi = 0x7fffffff;
             for (int l = lane; l < n; l += 32) {
-                float v = 0.f;
-                for (int a = 0; a < m; ++a) v += __bfloat162float(Qb[(size_t)l * m + a]) * (float)Zc[a * ld + c];
-                const float av = fabsf(v);
+                const float av = fabsf(Vs[l * kw + c]);
                 if (av > best || (av == best && l < bi)) { best = av; bi = l; }
             }
 #pragma unroll
@@ -524,14 +592,9 @@ __global__ void __launch_bounds__(256) k_rr(Src src, TcScratch sc, int n, int kw
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (lane == 0) {
-                float v = 0.f;
-                for (int a = 0; a < m; ++a) v += __bfloat162float(Qb[(size_t)bi * m + a]) * (float)Zc[a * ld + c];
-                sgn[c] = v < 0.f ? -1 : 1;
-            }
+            if (lane == 0) sgnf[c] = (bi < n && Vs[bi * kw + c] < 0.f) ? -1.f : 1.f;
         }
         __syncthreads();
-        // V^T (kw x n) and U = Y Z Sigma^-1 (rows x kw)
         float* vt_out;
         float* u_out;
         int64_t urows;
@@ -542,11 +605,16 @@ __global__ void __launch_bounds__(256) k_rr(Src src, TcScratch sc, int n, int kw
             urows = rows;
             float* sr = (float*)src.a.sr + (size_t)item * src.a.kq;
             for (int c = tid; c < src.a.kout; c += nt) {
-                const float s = c < kw ? sig[c] : 0.f;
-                if (c < kw) sr[c] = s;
-                ((float*)P.S_out)[c] = s;
+                const float sv = c < kw ? sig[c] : 0.f;
+                if (c < kw) sr[c] = sv;
+                ((float*)P.S_out)[c] = sv;
             }
             if (tid == 0 && P.rank) *P.rank = s_rank;
+            for (int e = tid; e < n * src.a.kout; e += nt) {
+                const int l = e / src.a.kout, c = e - (e / src.a.kout) * src.a.kout;
+                const float v = (c < kw && sig[c] > 0.f) ? sgnf[c] * Vs[l * kw + c] : 0.f;
+                ((float*)P.V_out)[(size_t)l * P.ldv + c] = v;
+            }
         } else {
             const int slot = src.c.slot0 + item;
             vt_out = (float*)src.c.vt + (size_t)slot * src.c.k * n;
@@ -557,33 +625,39 @@ __global__ void __launch_bounds__(256) k_rr(Src src, TcScratch sc, int n, int kw
         }
         for (int e = tid; e < kw * n; e += nt) {
             const int c = e / n, l = e - (e / n) * n;
-            float v = 0.f;
-            if (sig[c] > 0.f) {
-                for (int a = 0; a < m; ++a) v += __bfloat162float(Qb[(size_t)l * m + a]) * (float)Zc[a * ld + c];
-                v *= (float)sgn[c];
-            }
-            vt_out[e] = v;
+            vt_out[e] = sig[c] > 0.f ? sgnf[c] * Vs[l * kw + c] : 0.f;
+        }
+        // fold sign / sigma into Z so that U = Y Zsm
+        __syncthreads();
+        for (int e = tid; e < m * kw; e += nt) {
+            const int c = e % kw;
+            Zsm[e] = sig[c] > 0.f ? Zsm[e] * sgnf[c] / sig[c] : 0.f;
         }
         __syncthreads();
-        if constexpr (QUERY) {
-            const QPlan& P = src.a.plans[item];
-            for (int e = tid; e < n * src.a.kout; e += nt) {
-                const int l = e / src.a.kout, c = e - (e / src.a.kout) * src.a.kout;
-                ((float*)P.V_out)[(size_t)l * P.ldv + c] = c < kw ? vt_out[(size_t)c * n + l] : 0.f;
+        for (int r = tid; r < urows; r += nt) {
+            float yr[ZS_MAXM];
+            if (r < rows) {
+                const float4* y4 = reinterpret_cast<const float4*>(Y + (size_t)r * m);
+#pragma unroll
+                for (int a4 = 0; a4 < ZS_MAXM / 4; ++a4) {
+                    if (a4 * 4 >= m) break;
+                    const float4 v = __ldg(y4 + a4);
+                    yr[4 * a4] = v.x; yr[4 * a4 + 1] = v.y; yr[4 * a4 + 2] = v.z; yr[4 * a4 + 3] = v.w;
+                }
+            }
+            float* ur = u_out + (size_t)r * kw;
+            for (int c = 0; c < kw; ++c) {
+                float acc = 0.f;
+                if (r < rows) {
+#pragma unroll
+                    for (int a = 0; a < ZS_MAXM; ++a) {
+                        if (a >= m) break;
+                        acc += yr[a] * Zsm[a * kw + c];
+                    }
+                }
+                ur[c] = acc;
             }
         }
-        for (int e = tid; e < urows * kw; e += nt) {
-            const int r = e / kw, c = e - (e / kw) * kw;
-            float v = 0.f;
-            if (r < rows && sig[c] > 0.f) {
-                const float* yr = Y + (size_t)r * m;
-                TR d = 0;
-                for (int a = 0; a < m; ++a) d += (TR)yr[a] * Zc[a * ld + c];
-                v = (float)d / sig[c] * (float)sgn[c];
-            }
-            u_out[e] = v;
-        }
-        __syncthreads();
     }
 }
 

@@ -129,6 +129,31 @@ def test_batch_equals_single(plain):
         compare_query(outs[q], oracle.query(ost, int(ts[q]), int(te[q])), **F64, label=f"batch {q}")
 
 
+def test_graph_replay_equals_eager():
+    """Query batches replayed from the captured CUDA graph equal eager launches."""
+    from paper_1805_00754_gb300 import zoomsvd
+    w, A = _reduced("ragged_batch_f32", 12, 304)
+    st, exact = gpu_store(A, w.b, w.k, "f32")
+    T = A.shape[0]
+    ts, te = synthetic.queries(T, 24, 500, 20_000, seed=21)
+    zoomsvd.profile(True)                 # profiler on: eager launches
+    eager = st.query_batch(ts, te)
+    torch.cuda.synchronize()
+    zoomsvd.profile(False)
+    st.query_batch(ts, te)                # warm (eager) batch of this shape
+    graph1 = st.query_batch(ts, te)       # captured
+    graph2 = st.query_batch(ts[::-1].copy(), te[::-1].copy())   # replayed, new plans
+    sub = [3, 0, 17, 9, 11]                                       # replayed, fewer queries
+    graph3 = st.query_batch(ts[sub], te[sub])
+    torch.cuda.synchronize()
+    for q in range(len(ts)):
+        for a, b_ in [(eager[q], graph1[q]), (eager[q], graph2[len(ts) - 1 - q])]:
+            assert torch.equal(a.S, b_.S) and torch.equal(a.U, b_.U) and torch.equal(a.V, b_.V)
+    for i, q in enumerate(sub):
+        a, b_ = eager[q], graph3[i]
+        assert torch.equal(a.S, b_.S) and torch.equal(a.U, b_.U) and torch.equal(a.V, b_.V)
+
+
 def test_errors(plain):
     from paper_1805_00754_gb300 import ZsError
     w, A, st, ost = plain
