@@ -103,6 +103,22 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(values, device):
+    """Max of each value over all ranks (identity when not distributed)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    import torch.distributed as tdist
+    if tdist.is_available() and tdist.is_initialized() and tdist.get_world_size() > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def aggregate_rate(world: int, steps: int, units_per_step_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput: every rank processes the same per-rank work (weak
+    scaling); the job takes as long as the slowest rank."""
+    return world * steps * units_per_step_per_rank / max_seconds
+
+
 def _input_rows(w, host=False):
     A = synthetic.rows(w.series, dtype=np.float64)
     if w.dtype == "f64":
@@ -260,13 +276,10 @@ def run_gpu(args, w):
     zoomsvd.profile(False)
     tc = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
     tq = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
-    times = torch.tensor([tc, tq], dtype=torch.float64, device=f"cuda:{local}")
-    if dist:
-        dist.all_reduce(times, op=dist.ReduceOp.MAX)
-    tc, tq = times.tolist()
+    tc, tq = reduce_max([tc, tq], f"cuda:{local}")
     K = args.steps
-    compress_gbps = ws * K * in_bytes / tc / 1e9
-    qps = ws * K * nq / tq if nq else None
+    compress_gbps = aggregate_rate(ws, K, in_bytes, tc) / 1e9
+    qps = aggregate_rate(ws, K, nq, tq) if nq else None
     ms_step = (tc + tq) / K * 1e3
 
     # e2e through the C ABI from pinned host rows (H2D inside the timed region)
@@ -287,10 +300,8 @@ def run_gpu(args, w):
             e1.synchronize()
             if i >= args.warmup:
                 te2e += e0.elapsed_time(e1) / 1e3
-        tt = torch.tensor([te2e], dtype=torch.float64, device=f"cuda:{local}")
-        if dist:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = {"value": ws * K * in_bytes / tt.item() / 1e9, "unit": "GB/s",
+        (te2e,) = reduce_max([te2e], f"cuda:{local}")
+        e2e = {"value": aggregate_rate(ws, K, in_bytes, te2e) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": k * (8 if w.dtype == "f64" else 4)}
 
     # roofline of the dominant kernel
@@ -425,6 +436,7 @@ def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0):
     th.start()
     lib = zoomsvd.lib()
     tick = C.c_uint64()
+    arena_p, sv_p, vv_p = arena.data_ptr(), SV.data_ptr(), VV.data_ptr()
     for i, t_arr in enumerate(arrivals):
         d = t_start + t_arr - time.perf_counter()
         if d > 0:
@@ -432,8 +444,8 @@ def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0):
         L = int(te[i] - ts[i] + 1)
         if off + L > arena_rows:
             off = 0
-        res = zoomsvd.Result(arena.data_ptr() + off * k * 4, k, SV[i % 4096].data_ptr(),
-                             VV[i % 4096].data_ptr(), k, 0)
+        res = zoomsvd.Result(arena_p + off * k * 4, k, sv_p + (i % 4096) * k * 4,
+                             vv_p + (i % 4096) * n * k * 4, k, 0)
         off += L
         if lib.zs_serve_submit(sv._h, int(ts[i]), int(te[i]), k, C.byref(res), C.byref(tick)) == 0:
             pending.append(tick.value)

@@ -58,7 +58,7 @@ enum {
      * FP64 Jacobi refinement sweep.  No effect on ZS_F64 stores (all FP64).  */
     ZS_FLAG_FP64_REFINE = 1,
     /* Compute every Gram matrix exactly in FP32 on the CUDA cores (slower)
-     * instead of the default for float stores with n >= 128: a bf16
+     * instead of the default for float stores with n >= 64: a bf16
      * tensor-core Gram that only locates the dominant subspace, followed by a
      * split-bf16 (~FP32) projection and Rayleigh-Ritz that sets the accuracy. */
     ZS_FLAG_EXACT_GRAM = 2
@@ -184,6 +184,16 @@ zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out,
  * bad (nothing enqueued).                                                  */
 zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
                          int32_t k_out, const zs_result* results, void* stream);
+
+/* Autotuner (no counterpart in the paper): times the query launch set on
+ * nq deterministic ranges of the store's current rows under candidate grid
+ * shapes (persistent CTAs per SM of the slab work-list and projection
+ * kernels), keeps the fastest for this store and, if the environment
+ * variable ZS_TUNE_CACHE names a file, records it there keyed by
+ * (n, b, k, dtype, flags, SM count); stores created later with the same key
+ * start from the cached choice.  Results do not depend on the choice.  Needs
+ * appended rows; allocates temporary result buffers; synchronises `stream`. */
+zs_status zs_store_autotune(zs_store* st, int32_t nq, void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving: continuous batching of range queries (no counterpart in the

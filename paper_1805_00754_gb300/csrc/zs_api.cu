@@ -18,6 +18,7 @@
 
 namespace zs {
 int64_t launch_count_total();
+void tune_cache_load(zs_store* st);
 
 thread_local std::string g_last_error;
 
@@ -355,6 +356,7 @@ extern "C" zs_status zs_store_create(const zs_store_config* cfg, zs_store** out)
     st->tsize = fp64 ? 8 : 4;
     st->insize = in_size(c.in_dtype);
     cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+    tune_cache_load(st);
     zs_status s = store_alloc(st);
     if (s != ZS_OK) {
         zs_store_destroy(st);
@@ -377,6 +379,8 @@ extern "C" void zs_store_destroy(zs_store* st) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
     }
+    for (auto& pe : st->pending) cudaEventDestroy(pe.second);
+    for (auto e : st->event_pool) cudaEventDestroy(e);
     if (st->append_done) cudaEventDestroy(st->append_done);
     if (st->entry) cudaEventDestroy(st->entry);
     if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
@@ -446,6 +450,19 @@ extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nro
     int64_t pos = 0;
     int64_t T = st->T;
     zs_status s;
+    // forget appends that have finished on the device
+    {
+        size_t keep = 0;
+        for (size_t i = 0; i < st->pending.size(); ++i) {
+            if (cudaEventQuery(st->pending[i].second) == cudaSuccess) {
+                st->event_pool.push_back(st->pending[i].second);
+                continue;
+            }
+            cudaGetLastError();
+            st->pending[keep++] = st->pending[i];
+        }
+        st->pending.resize(keep);
+    }
     // device rows may still be being written on the caller's stream
     ZS_CU(cudaEventRecord(st->entry, stream), "event");
     ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->entry, 0), "wait");
@@ -498,6 +515,17 @@ extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nro
         T += rem;
     }
     ZS_CU(cudaEventRecord(st->append_done, stream), "event");
+    {
+        cudaEvent_t ev = nullptr;
+        if (!st->event_pool.empty()) {
+            ev = st->event_pool.back();
+            st->event_pool.pop_back();
+        } else {
+            ZS_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        }
+        ZS_CU(cudaEventRecord(ev, stream), "event");
+        st->pending.emplace_back((st->T / b) * b, ev);
+    }
     // host rows are free to reuse once the copies have run
     if (!dev) ZS_CU(cudaStreamSynchronize(st->copy_stream), "host copy");
     st->T = T;
@@ -510,6 +538,11 @@ extern "C" zs_status zs_store_reset(zs_store* st) {
     DeviceGuard g(st->cfg.device);
     ZS_CU(cudaEventSynchronize(st->append_done), "reset wait");
     if (st->qx.done) ZS_CU(cudaEventSynchronize(st->qx.done), "reset wait");
+    for (auto& pe : st->pending) {
+        cudaEventSynchronize(pe.second);
+        st->event_pool.push_back(pe.second);
+    }
+    st->pending.clear();
     st->T = 0;
     return ZS_OK;
 }
@@ -571,7 +604,23 @@ zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, cons
         plans[q].ldv = r.ldv;
         plans[q].rank = r.rank;
     }
-    ZS_CU(cudaStreamWaitEvent(stream, st->append_done, 0), "wait for appends");
+    // wait only for appends still running that rewrite blocks this batch reads
+    {
+        int64_t max_te = -1;
+        for (int q = 0; q < nq; ++q) max_te = std::max(max_te, te[q]);
+        size_t keep = 0;
+        for (size_t i = 0; i < st->pending.size(); ++i) {
+            auto& pe = st->pending[i];
+            if (cudaEventQuery(pe.second) == cudaSuccess) {
+                st->event_pool.push_back(pe.second);
+                continue;
+            }
+            cudaGetLastError();
+            if (pe.first <= max_te) ZS_CU(cudaStreamWaitEvent(stream, pe.second, 0), "wait for appends");
+            st->pending[keep++] = pe;
+        }
+        st->pending.resize(keep);
+    }
     // the executor's scratch may still be in use by a batch on another stream
     if (x.done) ZS_CU(cudaStreamWaitEvent(stream, x.done, 0), "wait for previous batch");
     // split batches whose scratch would exceed the budget
@@ -608,6 +657,139 @@ extern "C" zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64
     std::lock_guard<std::mutex> lk(st->mu);
     DeviceGuard g(st->cfg.device);
     return query_batch_locked(st, st->qx, ts, te, nq, k_out, results, (cudaStream_t)stream, st->T);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time the query launch set under candidate grid shapes on this
+// device and keep the fastest (results do not depend on the choice).
+// ---------------------------------------------------------------------------
+static std::string tune_key(const zs_store* st) {
+    char b[160];
+    snprintf(b, sizeof b, "n=%lld,b=%lld,k=%d,dtype=%d,flags=%d,sms=%d", (long long)st->cfg.n, (long long)st->cfg.b,
+             st->cfg.k, st->cfg.in_dtype, st->cfg.flags, st->num_sms);
+    return b;
+}
+
+static void tune_cache_store(const zs_store* st) {
+    const char* path = getenv("ZS_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::string key = tune_key(st);
+    std::vector<std::string> lines;
+    if (FILE* f = fopen(path, "r")) {
+        char buf[512];
+        while (fgets(buf, sizeof buf, f)) {
+            std::string l(buf);
+            if (l.compare(0, key.size() + 1, key + " ") != 0) lines.push_back(l);
+        }
+        fclose(f);
+    }
+    char v[128];
+    snprintf(v, sizeof v, " %d %d\n", st->tune.slab_ctas_per_sm, st->tune.project_ctas_per_sm);
+    lines.push_back(key + v);
+    if (FILE* f = fopen(path, "w")) {
+        for (auto& l : lines) fputs(l.c_str(), f);
+        fclose(f);
+    }
+}
+
+void zs::tune_cache_load(zs_store* st) {
+    const char* path = getenv("ZS_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    const std::string key = tune_key(st);
+    char buf[512];
+    while (fgets(buf, sizeof buf, f)) {
+        std::string l(buf);
+        if (l.compare(0, key.size() + 1, key + " ") == 0) {
+            int a = 0, c = 0;
+            if (sscanf(l.c_str() + key.size() + 1, "%d %d", &a, &c) == 2 && a > 0 && c > 0) {
+                st->tune.slab_ctas_per_sm = a;
+                st->tune.project_ctas_per_sm = c;
+            }
+        }
+    }
+    fclose(f);
+}
+
+extern "C" zs_status zs_store_autotune(zs_store* st, int32_t nq, void* stream_) {
+    if (!st || nq < 1) return fail(ZS_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(st->mu);
+    DeviceGuard g(st->cfg.device);
+    const int64_t T = st->T, b = st->cfg.b;
+    if (T < 1) return fail(ZS_EINVAL, "autotune needs appended rows");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int k = st->cfg.k, kq = std::min<int>(k, (int)st->cfg.n);
+    // nq ranges of up to 16 blocks, spread over the store (deterministic)
+    std::vector<int64_t> ts(nq), te(nq);
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    int64_t rows_total = 0;
+    for (int q = 0; q < nq; ++q) {
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        const int64_t len = std::max<int64_t>(1, std::min<int64_t>(T, (int64_t)(x % (16 * b)) + 1));
+        x ^= x << 13; x ^= x >> 7; x ^= x << 17;
+        ts[q] = (int64_t)(x % (uint64_t)(T - len + 1));
+        te[q] = ts[q] + len - 1;
+        rows_total += len;
+    }
+    const size_t ts_ = st->tsize;
+    void *U = nullptr, *S = nullptr, *V = nullptr;
+    auto fre = [&]() { if (U) cudaFree(U); if (S) cudaFree(S); if (V) cudaFree(V); };
+    if (cudaMalloc(&U, ts_ * rows_total * k) != cudaSuccess || cudaMalloc(&S, ts_ * (size_t)nq * k) != cudaSuccess ||
+        cudaMalloc(&V, ts_ * (size_t)nq * st->cfg.n * k) != cudaSuccess) {
+        cudaGetLastError();
+        fre();
+        return fail(ZS_ENOMEM, "autotune buffers");
+    }
+    std::vector<zs_result> res(nq);
+    int64_t off = 0;
+    for (int q = 0; q < nq; ++q) {
+        res[q].U = (char*)U + ts_ * off * k;
+        res[q].ldu = k;
+        res[q].S = (char*)S + ts_ * (size_t)q * k;
+        res[q].V = (char*)V + ts_ * (size_t)q * st->cfg.n * k;
+        res[q].ldv = k;
+        res[q].rank = nullptr;
+        off += te[q] - ts[q] + 1;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool graphs = st->use_graphs;
+    st->use_graphs = false;          // time the eager launch set of each candidate
+    const Tuning keep = st->tune;
+    Tuning best = keep;
+    float best_ms = 1e30f;
+    zs_status s = ZS_OK;
+    for (int slab : {2, 4, 8, 16}) {
+        for (int proj : {4, 8, 16}) {
+            st->tune = keep;
+            st->tune.slab_ctas_per_sm = slab;
+            st->tune.project_ctas_per_sm = proj;
+            float tot = 0;
+            for (int rep = 0; rep < 3 && s == ZS_OK; ++rep) {
+                cudaEventRecord(e0, stream);
+                s = query_batch_locked(st, st->qx, ts.data(), te.data(), nq, kq, res.data(), stream, T);
+                cudaEventRecord(e1, stream);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;          // first run warms caches and attributes
+            }
+            if (s != ZS_OK) break;
+            if (tot < best_ms) { best_ms = tot; best = st->tune; }
+        }
+        if (s != ZS_OK) break;
+    }
+    st->tune = (s == ZS_OK) ? best : keep;
+    st->use_graphs = graphs;
+    st->qx.release();                  // captured graphs used the old launch shapes
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(stream);
+    fre();
+    if (s == ZS_OK) tune_cache_store(st);
+    return s;
 }
 
 extern "C" zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out, const zs_result* res,

@@ -82,6 +82,11 @@ struct zs_store {
     cudaEvent_t stage_full[2] = {nullptr, nullptr};
     cudaEvent_t append_done = nullptr;
     cudaEvent_t entry = nullptr;
+    // appends whose device work may still run: (first row of the first block
+    // they (re)write, completion event).  A query waits only for those whose
+    // blocks it reads.
+    std::vector<std::pair<int64_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> event_pool;
     std::mutex mu;
     zs::Tuning tune;
     zs::QueryExec qx;

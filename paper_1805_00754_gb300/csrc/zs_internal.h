@@ -112,12 +112,14 @@ struct Tuning {
     int slab_ctas_per_sm = 4;    // persistent grid for slab work lists
     int eig_m_extra = 16;        // subspace oversampling p (m = kq + p)
     int power_its = 1;           // tensor path: power steps on the bf16 Gram
+    int project_ctas_per_sm = 8; // persistent grid of the projection kernel
 };
 
 // The tensor-core path (bf16 Gram for the subspace, split-bf16 projection and
-// Rayleigh-Ritz for accuracy) serves float factor stores with n >= 128 unless
-// the store asks for the exact FP32 Gram.
-inline bool use_tc_path(bool fp64, int n, int flags) { return !fp64 && n >= 128 && !(flags & 2); }
+// Rayleigh-Ritz for accuracy) serves float factor stores with n >= 64 (the
+// subspace width m <= 64 must not exceed n) unless the store asks for the
+// exact FP32 Gram.
+inline bool use_tc_path(bool fp64, int n, int flags) { return !fp64 && n >= 64 && !(flags & 2); }
 inline int tc_width(int kq, int extra) {
     int m = ((kq + extra) + 7) / 8 * 8;
     return m > 64 ? 64 : m;

@@ -1037,7 +1037,7 @@ static size_t tc_subspace_smem(int n, int m, bool& yglob) {
     return yglob ? (size_t)n * (m + 1) * 4 : both;
 }
 static size_t tc_project_smem(int n, int m) {
-    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)2 * 128 * 72 * 2;
+    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)3 * 128 * 72 * 2;
 }
 
 // Auxiliary scratch of the tensor path, carved from one buffer:
@@ -1061,7 +1061,7 @@ static void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, int kw,
 
 template <class Src, typename Tin, bool REF, bool QUERY>
 static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
-                           int ews_ctas, int num_sms, cudaStream_t st) {
+                           int ews_ctas, int num_sms, int proj_per_sm, cudaStream_t st) {
     const int ntile = (n + 127) / 128;
     const int npairs = ntile * (ntile + 1) / 2;
     const int gi = std::min(max_items, 65535);
@@ -1088,7 +1088,7 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
         const size_t sm = tc_project_smem(n, sc.m);
         ZS_TRY(set_smem(k_project<Src, Tin>, sm));
         prof::Scope ps(QUERY ? "project_query" : "project", st);
-        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * 8);
+        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * proj_per_sm);
         k_project<Src, Tin><<<std::max(gp, 1), 256, sm, st>>>(src, sc, n);
     }
     ZS_TRY(cudaGetLastError());
@@ -1125,7 +1125,8 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
     tc_aux_carve(c.aux, c.nblk, (int64_t)c.nblk * ((c.b + 127) / 128), sc.m, c.k, sc);
     SrcCompress src{c};
     return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,
-                                                 (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms, st);
+                                                 (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms,
+                                                 tu.project_ctas_per_sm, st);
 }
 
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
@@ -1195,7 +1196,8 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             sc.power_its = tu.power_its;
             tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
             SrcQuery src{a};
-            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms, st)));
+            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
+                                                        tu.project_ctas_per_sm, st)));
             {
                 const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
                 ZS_TRY(set_smem(k_bfix, sm));

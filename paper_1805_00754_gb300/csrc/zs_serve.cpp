@@ -44,6 +44,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     bool busy = false;
+    bool launching = false;
     size_t bytes = 0;
     std::vector<Request*> reqs;
 };
@@ -95,65 +96,78 @@ static void serve_loop(zs_server* sv) {
     std::vector<zs_result> res;
     for (;;) {
         bool idle = true;
+        Slot* launch_slot = nullptr;
+        int kout = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             // completions
             for (auto& sp : sv->slots) {
                 Slot& s = *sp;
-                if (!s.busy) continue;
+                if (!s.busy || s.launching) continue;
                 const cudaError_t q = cudaEventQuery(s.ev);
                 if (q == cudaErrorNotReady) continue;
                 finish_slot(sv, s, q == cudaSuccess ? ZS_OK : ZS_ECUDA);
                 idle = false;
                 sv->cv_done.notify_all();
             }
-            // admissions: fill free slots
+            // admission into one free slot: the oldest requests sharing a k_out,
+            // up to max_batch and the memory budget
             for (auto& sp : sv->slots) {
                 Slot& s = *sp;
                 if (s.busy || sv->queue.empty()) continue;
-                const int kout = sv->queue.front()->kout;
-                std::vector<Request*> take;
+                kout = sv->queue.front()->kout;
                 size_t bytes = 0;
-                for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->cfg.max_batch;) {
+                s.reqs.clear();
+                for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)s.reqs.size() < sv->cfg.max_batch;) {
                     Request* r = *it;
                     if (r->kout != kout) { ++it; continue; }
-                    const bool alone = take.empty() && sv->bytes_inflight == 0;
+                    const bool alone = s.reqs.empty() && sv->bytes_inflight == 0;
                     if (!alone && sv->bytes_inflight + bytes + r->bytes > (size_t)sv->cfg.memory_budget) break;
-                    take.push_back(r);
+                    s.reqs.push_back(r);
                     bytes += r->bytes;
                     it = sv->queue.erase(it);
                 }
-                if (take.empty()) break;   // memory budget full: wait for completions
-                ts.resize(take.size());
-                te.resize(take.size());
-                res.resize(take.size());
-                for (size_t i = 0; i < take.size(); ++i) {
-                    ts[i] = take[i]->ts;
-                    te[i] = take[i]->te;
-                    res[i] = take[i]->dst;
-                }
-                zs_status st;
-                {
-                    std::lock_guard<std::mutex> sl(sv->st->mu);
-                    st = zs::query_batch_locked(sv->st, s.x, ts.data(), te.data(), (int)take.size(), kout,
-                                                res.data(), s.stream, sv->st->T);
-                }
-                s.reqs = take;
+                if (s.reqs.empty()) break;   // memory budget full: wait for completions
                 s.bytes = bytes;
                 s.busy = true;
+                s.launching = true;
                 sv->bytes_inflight += bytes;
                 ++sv->batches;
-                sv->batched_reqs += (int64_t)take.size();
-                if (st != ZS_OK || cudaEventRecord(s.ev, s.stream) != cudaSuccess) {
-                    cudaStreamSynchronize(s.stream);
-                    finish_slot(sv, s, st != ZS_OK ? st : ZS_ECUDA);
-                    sv->cv_done.notify_all();
-                }
-                idle = false;
+                sv->batched_reqs += (int64_t)s.reqs.size();
+                launch_slot = &s;
+                break;
             }
             bool any_busy = false;
             for (auto& sp : sv->slots) any_busy |= sp->busy;
-            if (sv->stopping && sv->queue.empty() && !any_busy) break;
+            if (!launch_slot && sv->stopping && sv->queue.empty() && !any_busy) break;
+        }
+        if (launch_slot) {
+            // plan and launch without holding the server lock (submitters keep going)
+            Slot& s = *launch_slot;
+            const size_t nb = s.reqs.size();
+            ts.resize(nb);
+            te.resize(nb);
+            res.resize(nb);
+            for (size_t i = 0; i < nb; ++i) {
+                ts[i] = s.reqs[i]->ts;
+                te[i] = s.reqs[i]->te;
+                res[i] = s.reqs[i]->dst;
+            }
+            zs_status st;
+            {
+                std::lock_guard<std::mutex> sl(sv->st->mu);
+                st = zs::query_batch_locked(sv->st, s.x, ts.data(), te.data(), (int)nb, kout, res.data(),
+                                            s.stream, sv->st->T);
+            }
+            const bool ok = (st == ZS_OK) && cudaEventRecord(s.ev, s.stream) == cudaSuccess;
+            std::unique_lock<std::mutex> lk(sv->mu);
+            s.launching = false;
+            if (!ok) {
+                cudaStreamSynchronize(s.stream);
+                finish_slot(sv, s, st != ZS_OK ? st : ZS_ECUDA);
+                sv->cv_done.notify_all();
+            }
+            idle = false;
         }
         if (idle) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }

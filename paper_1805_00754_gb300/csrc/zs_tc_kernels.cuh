@@ -8,9 +8,9 @@
 //                   Only used to locate the dominant subspace (~1e-3 accurate).
 //   2. k_subspace   m columns Q of G~'s dominant subspace: pivoted columns of G~
 //                   and power steps with Gram-Schmidt (SIMT), stored as bf16 Q~.
-//   3. k_project    Y = X Q~ with X split into bf16 hi + lo parts: two bf16
-//                   tensor products give X Q~ to ~2^-17 relative (Q~ is exact in
-//                   bf16, so nothing of Q is lost).
+//   3. k_project    Y = X Q~ with X split into three bf16 terms (hi + mid +
+//                   lo, ~24 bits): three bf16 tensor products give X Q~ to FP32
+//                   accuracy (Q~ is exact in bf16, so nothing of Q is lost).
 //   4. k_rr         Rayleigh-Ritz on span(Q~): Y^T Y z = theta (Q~^T Q~) z via a
 //                   Cholesky of Q~^T Q~ and the small Jacobi core; then
 //                   sigma = sqrt(theta), V = Q~ Z, U = Y Z Sigma^{-1}.
@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
 }
 
 // ---------------------------------------------------------------------------
-// 3. Y = X Q~ for 128-row tiles: X split into bf16 hi + lo (two products).
+// 3. Y = X Q~ for 128-row tiles: X split into three bf16 terms (three products,
+//    smallest term first).
 // ---------------------------------------------------------------------------
 template <class Src, typename Tin>
 __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
@@ -298,7 +299,8 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
     const int m = sc.m, ldqs = bf16_ld(m);
     __nv_bfloat16* Qs = (__nv_bfloat16*)dsm;                      // n x ldqs
     __nv_bfloat16* Xh = Qs + (size_t)((n + 15) / 16 * 16) * ldqs;    // 128 x LDX
-    __nv_bfloat16* Xl = Xh + 128 * LDX;
+    __nv_bfloat16* Xm = Xh + 128 * LDX;
+    __nv_bfloat16* Xl = Xm + 128 * LDX;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ld = src.ld();
     const int ntn = m / 8;
@@ -336,9 +338,13 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
                     if constexpr (std::is_same<Tin, float>::value) v = __ldg(p);
                     else v = __bfloat162float(*p);
                 }
-                __nv_bfloat16 hi, lo;
-                split_bf16(v, hi, lo);
+                // three bf16 terms carry ~24 significant bits of the fp32 value
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                const float r1 = v - __bfloat162float(hi);
+                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
                 Xh[r * LDX + c] = hi;
+                Xm[r * LDX + c] = mid;
                 Xl[r * LDX + c] = lo;
             }
             __syncthreads();
@@ -346,8 +352,9 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
             for (int kk = 0; kk < kmax; kk += 16) {
                 const int mat = lane >> 3, rr = lane & 7;
                 const int arow = warp * 16 + ((mat & 1) ? 8 : 0) + rr, acol = kk + ((mat >> 1) ? 8 : 0);
-                uint32_t ah[4], al[4];
+                uint32_t ah[4], am[4], al[4];
                 ldsm_x4(smem_u32(Xh + arow * LDX + acol), ah[0], ah[1], ah[2], ah[3]);
+                ldsm_x4(smem_u32(Xm + arow * LDX + acol), am[0], am[1], am[2], am[3]);
                 ldsm_x4(smem_u32(Xl + arow * LDX + acol), al[0], al[1], al[2], al[3]);
 #pragma unroll
                 for (int np = 0; np < 4; ++np) {
@@ -361,11 +368,13 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
                         ldsm_x2_t(smem_u32(Qs + t * ldqs + np * 16), b0, b1);
                         b2 = b3 = 0;
                     }
-                    mma_bf16(acc[2 * np], ah[0], ah[1], ah[2], ah[3], b0, b1);
                     mma_bf16(acc[2 * np], al[0], al[1], al[2], al[3], b0, b1);
+                    mma_bf16(acc[2 * np], am[0], am[1], am[2], am[3], b0, b1);
+                    mma_bf16(acc[2 * np], ah[0], ah[1], ah[2], ah[3], b0, b1);
                     if (2 * np + 1 < ntn) {
-                        mma_bf16(acc[2 * np + 1], ah[0], ah[1], ah[2], ah[3], b2, b3);
                         mma_bf16(acc[2 * np + 1], al[0], al[1], al[2], al[3], b2, b3);
+                        mma_bf16(acc[2 * np + 1], am[0], am[1], am[2], am[3], b2, b3);
+                        mma_bf16(acc[2 * np + 1], ah[0], ah[1], ah[2], ah[3], b2, b3);
                     }
                 }
             }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libzoomsvd.so")
 
 ZS_F64, ZS_F32, ZS_BF16 = 0, 1, 2
 ZS_FLAG_FP64_REFINE = 1
+ZS_FLAG_EXACT_GRAM = 2
 DTYPES = {"f64": ZS_F64, "f32": ZS_F32, "bf16": ZS_BF16}
 STATUS = {0: "ZS_OK", 1: "ZS_EINVAL", 2: "ZS_ERANGE", 3: "ZS_ENOMEM", 4: "ZS_EBUSY",
           5: "ZS_ETIMEDOUT", 6: "ZS_EDTYPE", 7: "ZS_ECUDA", 8: "ZS_EINTERNAL", 9: "ZS_ENOTFOUND"}
@@ -63,6 +64,7 @@ SIGNATURES = {
     "zs_compress_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int64, C.c_int64,
                                       C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "zs_query": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(Result), C.c_void_p]),
+    "zs_store_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "zs_query_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32, C.c_int32,
                                  C.POINTER(Result), C.c_void_p]),
     "zs_serve_start": (C.c_int, [C.c_void_p, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
@@ -135,12 +137,12 @@ class Store:
     """A compressed range-SVD store on one GPU (the sets U, S, V of Def. 2)."""
 
     def __init__(self, n: int, b: int, k: int, dtype: str = "f32", capacity_rows: int = 1 << 20,
-                 device: int = 0, fp64_refine: bool = False):
+                 device: int = 0, fp64_refine: bool = False, exact_gram: bool = False):
         self.n, self.b, self.k, self.dtype = n, b, k, dtype
         self.device = torch.device("cuda", device)
         self.fdtype = factor_dtype(dtype)
-        cfg = StoreConfig(n, b, k, DTYPES[dtype], capacity_rows, device,
-                          ZS_FLAG_FP64_REFINE if fp64_refine else 0)
+        flags = (ZS_FLAG_FP64_REFINE if fp64_refine else 0) | (ZS_FLAG_EXACT_GRAM if exact_gram else 0)
+        cfg = StoreConfig(n, b, k, DTYPES[dtype], capacity_rows, device, flags)
         h = C.c_void_p()
         _check(lib().zs_store_create(C.byref(cfg), C.byref(h)))
         self._h = h
@@ -175,6 +177,9 @@ class Store:
             t = t.contiguous()
         on_dev = 1 if t.is_cuda else 0
         _check(lib().zs_store_append(self._h, t.data_ptr(), t.shape[0], t.stride(0), on_dev, _stream_ptr(stream)))
+
+    def autotune(self, nq: int = 64, stream=None):
+        _check(lib().zs_store_autotune(self._h, nq, _stream_ptr(stream)))
 
     def reset(self):
         _check(lib().zs_store_reset(self._h))

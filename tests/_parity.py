@@ -19,11 +19,11 @@ def device_rows(A64: np.ndarray, dtype: str):
     return torch.from_numpy(bits.view(np.int16)).cuda(), synthetic.bf16_bits_to_f64(bits)
 
 
-def gpu_store(A64, b, k, dtype, refine=False, capacity=None):
+def gpu_store(A64, b, k, dtype, refine=False, capacity=None, exact_gram=False):
     from paper_1805_00754_gb300 import Store
     rows, exact = device_rows(A64, dtype)
     st = Store(n=A64.shape[1], b=b, k=k, dtype=dtype, capacity_rows=capacity or A64.shape[0],
-               fp64_refine=refine)
+               fp64_refine=refine, exact_gram=exact_gram)
     st.append(rows)
     torch.cuda.synchronize()
     return st, exact
@@ -85,10 +85,11 @@ def compare_query(out, ref, s_tol, vec_tol, gap=1e-4, orth_tol=None, label=""):
     if orth_tol is not None and rank:
         # Gram-route accuracy model: U columns built as M V Sigma^-1 carry an
         # orthonormality error ~ eps (sigma_1 / sigma_j)^2.  Well-conditioned
-        # columns (sigma_j >= 1e-2 sigma_1) must meet orth_tol; all live
-        # columns must meet that model with a factor-100 margin.
+        # columns (sigma_j >= 1e-2 sigma_1 in FP64, >= 5e-2 sigma_1 in FP32)
+        # must meet orth_tol; all live columns must meet that model with a
+        # factor-100 margin.
         eps = 2.2e-16 if out.U.dtype == torch.float64 else 1.2e-7
-        good = int(np.sum(s[:rank] >= 1e-2 * s[0]))
+        good = int(np.sum(s[:rank] >= (1e-2 if eps < 1e-10 else 5e-2) * s[0]))
         Ug, Vl = U[:, :good], V[:, :rank]
         eu = np.max(np.abs(Ug.T @ Ug - np.eye(good))) if good else 0.0
         ev = np.max(np.abs(Vl.T @ Vl - np.eye(rank)))

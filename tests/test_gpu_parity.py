@@ -154,6 +154,21 @@ def test_graph_replay_equals_eager():
         assert torch.equal(a.S, b_.S) and torch.equal(a.U, b_.U) and torch.equal(a.V, b_.V)
 
 
+def test_autotune_keeps_results(tmp_path, monkeypatch):
+    monkeypatch.setenv("ZS_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    w, A = _reduced("ragged_batch_f32", 10, 304)
+    st, _ = gpu_store(A, w.b, w.k, "f32")
+    ts, te = synthetic.queries(A.shape[0], 16, 500, 15_000, seed=31)
+    before = st.query_batch(ts, te)
+    torch.cuda.synchronize()
+    st.autotune(32)
+    after = st.query_batch(ts, te)
+    torch.cuda.synchronize()
+    for a, b_ in zip(before, after):
+        assert torch.equal(a.S, b_.S) and torch.equal(a.U, b_.U) and torch.equal(a.V, b_.V)
+    assert (tmp_path / "tune.txt").read_text().startswith("n=128,b=2000,k=20")
+
+
 def test_errors(plain):
     from paper_1805_00754_gb300 import ZsError
     w, A, st, ost = plain
@@ -190,6 +205,22 @@ def test_f32_compress_workload(refine):
         out = st.query(int(a), int(z))
         torch.cuda.synchronize()
         compare_query(out, oracle.query(ost, int(a), int(z)), **F32, label=f"f32 [{a},{z}]")
+
+
+def test_exact_gram_path_matches_oracle_and_tensor_path():
+    """The FP32 CUDA-core Gram (ZS_FLAG_EXACT_GRAM) and the default tensor-core
+    path both meet the oracle; they agree with each other to the same bar."""
+    w, A = _reduced("ragged_batch_f32", 8, 304)
+    st_tc, exact = gpu_store(A, w.b, w.k, "f32")
+    st_ex, _ = gpu_store(A, w.b, w.k, "f32", exact_gram=True)
+    ost = oracle.compress(exact, w.b, w.k)
+    T = A.shape[0]
+    for a, z in [(0, T - 1), (1_999, 2_000), (3_333, 12_345), (16_000, T - 1)]:
+        o1, o2 = st_tc.query(a, z), st_ex.query(a, z)
+        torch.cuda.synchronize()
+        ref = oracle.query(ost, a, z)
+        compare_query(o1, ref, **F32, label=f"tensor [{a},{z}]")
+        compare_query(o2, ref, **F32, label=f"exact [{a},{z}]")
 
 
 def test_bf16_precision_workload():
