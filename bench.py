@@ -227,6 +227,10 @@ def run_gpu(args, w):
     import paper_1805_00754_gb300 as zs
     from paper_1805_00754_gb300 import zoomsvd
 
+    if args.rows:
+        # smaller case of the same workload (profiling captures)
+        import dataclasses
+        w = dataclasses.replace(w, series=dataclasses.replace(w.series, T=args.rows))
     T, n, b, k = w.series.T, w.series.n, w.b, w.k
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
     A = _input_rows(w)
@@ -475,6 +479,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")
     args = ap.parse_args()
     w = synthetic.WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -19,6 +19,7 @@
 namespace zs {
 int64_t launch_count_total();
 void tune_cache_load(zs_store* st);
+void prune_pending(zs_store* st);
 
 thread_local std::string g_last_error;
 
@@ -131,6 +132,21 @@ size_t QueryExec::bytes_for(const zs_store& st, int nq, int64_t nslab, int kq) {
     const size_t m = 64;
     return tc_aux_bytes(nq, (int64_t)nslab * k / 128 + nq, 64, kq) + ts * (nslab * k * n + (size_t)nq * n * n + (size_t)nq * kq * (n + 1) + 2 * (size_t)nq * k * k +
                  nslab * k * kq + nslab * k * m + (size_t)nq * n * m / 2) + sizeof(QPlan) * nq;
+}
+
+// Drop the appends that have finished on the device.
+void prune_pending(zs_store* st) {
+    size_t keep = 0;
+    for (size_t i = 0; i < st->pending.size(); ++i) {
+        const cudaError_t q = cudaEventQuery(st->pending[i].second);
+        if (q == cudaSuccess) {
+            st->event_pool.push_back(st->pending[i].second);
+            continue;
+        }
+        if (q != cudaErrorNotReady) cudaGetLastError();
+        st->pending[keep++] = st->pending[i];
+    }
+    st->pending.resize(keep);
 }
 
 // ---------------------------------------------------------------------------
@@ -314,6 +330,26 @@ static zs_status store_alloc(zs_store* st) {
     st->stage_blocks = (int)std::max<size_t>(1, std::min<size_t>(st->stage_budget / blk_bytes, st->gchunk));
     for (int i = 0; i < 2; ++i)
         if ((s = al(&st->stage[i], blk_bytes * st->stage_blocks, "host staging")) != ZS_OK) return s;
+    // append pipeline slots: one block of staging and scratch each
+    {
+        const size_t mt = use_tc_path(st->fp64, (int)c.n, c.flags) ? tc_width(c.k, st->tune.eig_m_extra) : 0;
+        for (int i = 0; i < zs_store::kPipe; ++i) {
+            auto& ps = st->pipe[i];
+            if ((s = al(&ps.stage, blk_bytes, "append pipeline staging")) != ZS_OK) return s;
+            if ((s = al(&ps.G, gper, "append pipeline gram")) != ZS_OK) return s;
+            if ((s = al(&ps.ews, eig_ws_bytes((int)c.n, st->fp64, 1), "append pipeline workspace")) != ZS_OK) return s;
+            if (mt) {
+                if ((s = al(&ps.qb, 2 * mt * (size_t)c.n, "append pipeline bases")) != ZS_OK) return s;
+                if ((s = al(&ps.ys, 4 * mt * (size_t)c.b, "append pipeline projections")) != ZS_OK) return s;
+                if ((s = al(&ps.aux, tc_aux_bytes(1, (c.b + 127) / 128, (int)mt, c.k), "append pipeline RR")) != ZS_OK)
+                    return s;
+            }
+            ZS_CU(cudaStreamCreateWithFlags(&ps.stream, cudaStreamNonBlocking), "stream");
+            ZS_CU(cudaEventCreateWithFlags(&ps.staged, cudaEventDisableTiming), "event");
+            ZS_CU(cudaEventCreateWithFlags(&ps.free, cudaEventDisableTiming), "event");
+            ZS_CU(cudaEventRecord(ps.free, ps.stream), "event");
+        }
+    }
     ZS_CU(cudaMemset(st->U, 0, ts * nb * c.b * c.k), "memset");
     ZS_CU(cudaMemset(st->sig, 0, ts * nb * c.k), "memset");
     ZS_CU(cudaMemset(st->vt, 0, ts * nb * c.k * c.n), "memset");
@@ -379,6 +415,13 @@ extern "C" void zs_store_destroy(zs_store* st) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
     }
+    for (auto& ps : st->pipe) {
+        if (ps.stream) cudaStreamSynchronize(ps.stream);
+        f(ps.stage); f(ps.G); f(ps.qb); f(ps.ys); f(ps.aux); f(ps.ews);
+        if (ps.staged) cudaEventDestroy(ps.staged);
+        if (ps.free) cudaEventDestroy(ps.free);
+        if (ps.stream) cudaStreamDestroy(ps.stream);
+    }
     for (auto& pe : st->pending) cudaEventDestroy(pe.second);
     for (auto e : st->event_pool) cudaEventDestroy(e);
     if (st->append_done) cudaEventDestroy(st->append_done);
@@ -391,10 +434,11 @@ extern "C" void zs_store_destroy(zs_store* st) {
 // Storage phase.
 // ---------------------------------------------------------------------------
 static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64_t rows_total, int nblk,
-                                 int64_t slot0, cudaStream_t stream) {
+                                 int64_t slot0, cudaStream_t stream, const zs_store::PipeSlot* ps = nullptr) {
     const zs_store_config& c = st->cfg;
-    for (int j0 = 0; j0 < nblk; j0 += st->gchunk) {
-        const int nb = std::min(st->gchunk, nblk - j0);
+    const int chunk = ps ? 1 : st->gchunk;
+    for (int j0 = 0; j0 < nblk; j0 += chunk) {
+        const int nb = std::min(chunk, nblk - j0);
         CompressChunk ch;
         memset(&ch, 0, sizeof ch);
         ch.A = (const char*)A + (size_t)j0 * c.b * lda * st->insize;
@@ -415,6 +459,14 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.qb = st->qb;
         ch.ys = st->ys;
         ch.aux = st->aux;
+        if (ps) {
+            ch.G = ps->G;
+            ch.qb = ps->qb;
+            ch.ys = ps->ys;
+            ch.aux = ps->aux;
+            ch.ews = ps->ews;
+            ch.ews_ctas = 1;
+        }
         cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, stream);
         if (e != cudaSuccess) return cuda_fail(e, "compression kernels");
     }
@@ -450,22 +502,41 @@ extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nro
     int64_t pos = 0;
     int64_t T = st->T;
     zs_status s;
-    // forget appends that have finished on the device
-    {
-        size_t keep = 0;
-        for (size_t i = 0; i < st->pending.size(); ++i) {
-            if (cudaEventQuery(st->pending[i].second) == cudaSuccess) {
-                st->event_pool.push_back(st->pending[i].second);
-                continue;
-            }
-            cudaGetLastError();
-            st->pending[keep++] = st->pending[i];
-        }
-        st->pending.resize(keep);
-    }
+    prune_pending(st);
     // device rows may still be being written on the caller's stream
     ZS_CU(cudaEventRecord(st->entry, stream), "event");
     ZS_CU(cudaStreamWaitEvent(st->copy_stream, st->entry, 0), "wait");
+    // short appends of whole blocks with no open block: pipeline them
+    if (T % b == 0 && nrows % b == 0 && nrows / b <= zs_store::kPipe) {
+        for (int64_t j = 0; j < nrows / b; ++j) {
+            auto& ps = st->pipe[st->pipe_next];
+            st->pipe_next = (st->pipe_next + 1) % zs_store::kPipe;
+            // the caller's stream copies the block into the slot once the slot's
+            // previous compression is done; compression then runs on the slot's stream
+            ZS_CU(cudaStreamWaitEvent(stream, ps.free, 0), "wait");
+            ZS_CU(cudaMemcpy2DAsync(ps.stage, es * c.n, (const char*)rows + es * j * b * ld, es * ld, es * c.n, b,
+                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream),
+                  "row copy");
+            ZS_CU(cudaEventRecord(ps.staged, stream), "event");
+            ZS_CU(cudaStreamWaitEvent(ps.stream, ps.staged, 0), "wait");
+            if ((s = compress_blocks(st, ps.stage, c.n, b, 1, T / b, ps.stream, &ps)) != ZS_OK) return s;
+            ZS_CU(cudaEventRecord(ps.free, ps.stream), "event");
+            cudaEvent_t ev = nullptr;
+            if (!st->event_pool.empty()) {
+                ev = st->event_pool.back();
+                st->event_pool.pop_back();
+            } else {
+                ZS_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+            }
+            ZS_CU(cudaEventRecord(ev, ps.stream), "event");
+            st->pending.emplace_back(T, ev);
+            ZS_CU(cudaEventRecord(st->append_done, ps.stream), "event");
+            T += b;
+        }
+        if (!dev) ZS_CU(cudaStreamSynchronize(stream), "host copy");
+        st->T = T;
+        return ZS_OK;
+    }
     // (1) extend the open block
     const int64_t tail_rows = T % b;
     if (tail_rows > 0) {
@@ -568,6 +639,7 @@ extern "C" zs_status zs_store_export_block(const zs_store* st_, int64_t i, void*
     DeviceGuard g(st->cfg.device);
     cudaStream_t s = (cudaStream_t)stream_;
     ZS_CU(cudaStreamWaitEvent(s, st->append_done, 0), "wait");
+    for (auto& pe : st->pending) ZS_CU(cudaStreamWaitEvent(s, pe.second, 0), "wait");
     const int64_t r = std::min(b, T - i * b);
     const size_t ts = st->tsize;
     if (U) ZS_CU(cudaMemcpyAsync(U, (char*)st->U + ts * i * b * k, ts * r * k, cudaMemcpyDeviceToDevice, s), "copy");
@@ -605,21 +677,14 @@ zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, cons
         plans[q].rank = r.rank;
     }
     // wait only for appends still running that rewrite blocks this batch reads
+    // (short appends run on several pipeline streams, so every such append's
+    // event is waited for; the list holds only appends not yet finished)
     {
         int64_t max_te = -1;
         for (int q = 0; q < nq; ++q) max_te = std::max(max_te, te[q]);
-        size_t keep = 0;
-        for (size_t i = 0; i < st->pending.size(); ++i) {
-            auto& pe = st->pending[i];
-            if (cudaEventQuery(pe.second) == cudaSuccess) {
-                st->event_pool.push_back(pe.second);
-                continue;
-            }
-            cudaGetLastError();
+        prune_pending(st);
+        for (auto& pe : st->pending)
             if (pe.first <= max_te) ZS_CU(cudaStreamWaitEvent(stream, pe.second, 0), "wait for appends");
-            st->pending[keep++] = pe;
-        }
-        st->pending.resize(keep);
     }
     // the executor's scratch may still be in use by a batch on another stream
     if (x.done) ZS_CU(cudaStreamWaitEvent(stream, x.done, 0), "wait for previous batch");

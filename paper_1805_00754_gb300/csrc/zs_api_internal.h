@@ -87,6 +87,18 @@ struct zs_store {
     // blocks it reads.
     std::vector<std::pair<int64_t, cudaEvent_t>> pending;
     std::vector<cudaEvent_t> event_pool;
+    // append pipeline: a short append of whole blocks is staged block by block
+    // into one of kPipe slots, each compressed on its own stream with its own
+    // one-block scratch, so consecutive small appends overlap on the device
+    static constexpr int kPipe = 4;
+    struct PipeSlot {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t staged = nullptr;     // rows copied into stage
+        cudaEvent_t free = nullptr;       // compression of the slot finished
+        void* stage = nullptr;            // b x n input rows
+        void *G = nullptr, *qb = nullptr, *ys = nullptr, *aux = nullptr, *ews = nullptr;
+    } pipe[kPipe];
+    int pipe_next = 0;
     std::mutex mu;
     zs::Tuning tune;
     zs::QueryExec qx;

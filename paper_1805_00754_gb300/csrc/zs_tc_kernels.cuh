@@ -102,7 +102,7 @@ __device__ __forceinline__ float4 ld4<float>(const float* p) { return __ldg(rein
 //    of tiles), rows streamed in chunks of 32 through shared memory.
 // ---------------------------------------------------------------------------
 template <class Src, typename Tin>
-__global__ void __launch_bounds__(256, 2) k_gram_lo(Src src, TcScratch sc, int n) {
+__global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n) {
     constexpr int LDS = 136;                        // bf16_ld(128)
     __shared__ __align__(16) __nv_bfloat16 XI[32 * LDS];
     __shared__ __align__(16) __nv_bfloat16 XJ[32 * LDS];
@@ -127,15 +127,21 @@ __global__ void __launch_bounds__(256, 2) k_gram_lo(Src src, TcScratch sc, int n
             for (int b = 0; b < 4; ++b)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-        for (int r0 = 0; r0 < rows; r0 += 32) {
-            __syncthreads();
-            // stage two column panels of 32 rows as bf16
-            for (int pnl = 0; pnl < (diag ? 1 : 2); ++pnl) {
+        // Each thread owns 4 groups of 4 consecutive columns per panel and keeps
+        // the next 32-row chunk in registers while the current one is multiplied.
+        const int npnl = diag ? 1 : 2;
+        float pre[2][4][4];
+        auto fetch = [&](int r0) {
+#pragma unroll
+            for (int pnl = 0; pnl < 2; ++pnl) {
+                if (pnl >= npnl) break;
                 const int P0 = pnl ? J0 : I0;
-                __nv_bfloat16* D = pnl ? XJ : XI;
-                for (int f = tid; f < 32 * 32; f += 256) {
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int f = tid + g * 256;
                     const int r = f >> 5, c = (f & 31) * 4, gr = r0 + r, gc = P0 + c;
-                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+                    float* v = pre[pnl][g];
+                    v[0] = v[1] = v[2] = v[3] = 0.f;
                     if (gr < rows) {
                         const Tin* src_p = X + (int64_t)gr * ld + gc;
                         if constexpr (std::is_same<Tin, float>::value) {
@@ -153,12 +159,28 @@ __global__ void __launch_bounds__(256, 2) k_gram_lo(Src src, TcScratch sc, int n
                                 if (gc + e < n) v[e] = __bfloat162float(src_p[e]);
                         }
                     }
+                }
+            }
+        };
+        fetch(0);
+        for (int r0 = 0; r0 < rows; r0 += 32) {
+            __syncthreads();
+#pragma unroll
+            for (int pnl = 0; pnl < 2; ++pnl) {
+                if (pnl >= npnl) break;
+                __nv_bfloat16* D = pnl ? XJ : XI;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int f = tid + g * 256;
+                    const int r = f >> 5, c = (f & 31) * 4;
+                    const float* v = pre[pnl][g];
                     uint32_t* dp = reinterpret_cast<uint32_t*>(D + r * LDS + c);
                     dp[0] = pack_bf16(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
                     dp[1] = pack_bf16(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
                 }
             }
             __syncthreads();
+            if (r0 + 32 < rows) fetch(r0 + 32);     // in flight during the MMAs
             const __nv_bfloat16* BJ = diag ? XI : XJ;
 #pragma unroll
             for (int kk = 0; kk < 32; kk += 16) {
@@ -328,26 +350,59 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
         for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        // each thread stages 8 groups of 4 consecutive values per 128 x 64 chunk;
+        // the next chunk's loads are issued before the current chunk's MMAs
+        const bool xal = std::is_same<Tin, float>::value && (ld % 4 == 0) &&
+                         ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        float pre[8][4];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int f = tid + g * 256;
+                const int r = f >> 4, c = (f & 15) * 4;
+                float* v = pre[g];
+                v[0] = v[1] = v[2] = v[3] = 0.f;
+                if (r0 + r < rows) {
+                    const Tin* p = X + (int64_t)(r0 + r) * ld + k0 + c;
+                    if constexpr (std::is_same<Tin, float>::value) {
+                        if (xal && k0 + c + 3 < n) {
+                            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+                            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (k0 + c + e < n) v[e] = __ldg(p + e);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (k0 + c + e < n) v[e] = __bfloat162float(p[e]);
+                    }
+                }
+            }
+        };
+        fetch(0);
         for (int k0 = 0; k0 < n; k0 += KC) {
             __syncthreads();
-            for (int e = tid; e < 128 * KC; e += 256) {
-                const int r = e / KC, c = e - (e / KC) * KC;
-                float v = 0.f;
-                if (r0 + r < rows && k0 + c < n) {
-                    const Tin* p = X + (int64_t)(r0 + r) * ld + k0 + c;
-                    if constexpr (std::is_same<Tin, float>::value) v = __ldg(p);
-                    else v = __bfloat162float(*p);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const int f = tid + g * 256;
+                const int r = f >> 4, c = (f & 15) * 4;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    // three bf16 terms carry ~24 significant bits of the fp32 value
+                    const float v = pre[g][e];
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                    const float r1 = v - __bfloat162float(hi);
+                    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+                    Xh[r * LDX + c + e] = hi;
+                    Xm[r * LDX + c + e] = mid;
+                    Xl[r * LDX + c + e] = lo;
                 }
-                // three bf16 terms carry ~24 significant bits of the fp32 value
-                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                const float r1 = v - __bfloat162float(hi);
-                const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-                Xh[r * LDX + c] = hi;
-                Xm[r * LDX + c] = mid;
-                Xl[r * LDX + c] = lo;
             }
             __syncthreads();
+            if (k0 + KC < n) fetch(k0 + KC);
             const int kmax = min(KC, ((n - k0) + 15) / 16 * 16);
             for (int kk = 0; kk < kmax; kk += 16) {
                 const int mat = lane >> 3, rr = lane & 7;

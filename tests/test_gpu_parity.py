@@ -15,7 +15,7 @@ from tests._parity import compare_query, gpu_store, sigma_rel_err, _to_np
 pytestmark = pytest.mark.gpu
 
 F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-10)
-F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=1e-4)
+F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=5e-4)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -114,6 +114,30 @@ def test_ragged_tail_and_piecewise_append():
         torch.cuda.synchronize()
         assert torch.equal(o1.S, o2.S) and torch.equal(o1.U, o2.U) and torch.equal(o1.V, o2.V)
         compare_query(o1, oracle.query(ost, ts, te), **F64, label=f"tail [{ts},{te}]")
+
+
+def test_pipelined_small_appends_with_interleaved_queries():
+    """Appends of 1-3 whole blocks go through the append pipeline (several
+    streams); queries issued in between see every appended row, and the final
+    store equals the one built by a single append."""
+    w, A = _reduced("ragged_batch_f32", 9, 0)
+    one, exact = gpu_store(A, w.b, w.k, "f32")
+    from paper_1805_00754_gb300 import Store
+    st = Store(n=128, b=w.b, k=w.k, dtype="f32", capacity_rows=A.shape[0])
+    dev = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float32)).cuda()
+    ost = oracle.compress(exact, w.b, w.k)
+    row = 0
+    for nb in [1, 2, 1, 3, 2]:
+        st.append(dev[row:row + nb * w.b])
+        row += nb * w.b
+        out = st.query(max(0, row - 3 * w.b // 2), row - 1)     # touches the newest blocks
+        torch.cuda.synchronize()
+        compare_query(out, oracle.query(ost, max(0, row - 3 * w.b // 2), row - 1), **F32, label=f"pipe {row}")
+    assert st.info()[:2] == (A.shape[0], 9)
+    for a, z in [(0, A.shape[0] - 1), (2_500, 13_333)]:
+        o1, o2 = one.query(a, z), st.query(a, z)
+        torch.cuda.synchronize()
+        assert torch.equal(o1.S, o2.S) and torch.equal(o1.U, o2.U) and torch.equal(o1.V, o2.V)
 
 
 def test_batch_equals_single(plain):
