@@ -854,17 +854,18 @@ __global__ void __launch_bounds__(256) k_ur(QueryArgs a) {
 }
 
 // Lift (Eq. 9): output rows of each slab = U_i(rows) C_slab, zero past k_q.
-// A group of G lanes owns one output row; lane c of the group keeps column c
-// of C_slab in registers, reads the row of U_i (broadcast within the group)
-// and writes out[row][c] (coalesced along c).
-template <typename T, int KMAX>
-__global__ void __launch_bounds__(256) k_lift(QueryArgs a, int grp) {
+// One output row per lane: the lane reads its row of U_i (contiguous, vector
+// loads), multiplies by C_slab held in shared memory (read as warp-wide
+// broadcasts) and writes its contiguous output row; RU rows per lane are in
+// flight at once.
+template <typename T, int KMAX, int QMAX>
+__global__ void __launch_bounds__(256) k_lift(QueryArgs a) {
+    __shared__ __align__(16) T Cs[KMAX * QMAX];
     const int k = a.k, kq = a.kq, kout = a.kout;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int c = lane % grp, sub = lane / grp, rows_per_warp = 32 / grp;
+    const int tid = threadIdx.x;
     const int nq = a.hdr->nq;
     const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
-    const bool vec = (sizeof(T) == 4) && (k % 4 == 0);
+    constexpr int RU = 2;
     for (int64_t s = blockIdx.x; s < total; s += gridDim.x) {
         const int q = find_query(a.slab_prefix, nq, s);
         const QPlan& P = a.plans[q];
@@ -872,53 +873,59 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a, int grp) {
         const BlockRange br = slab_rows(P, t, a.b, Trows);
         const T* U = (const T*)a.U + (int64_t)br.blk * a.b * k;
         const T* Cg = (const T*)a.C + s * k * kq;
-        T cc[KMAX];
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) cc[j] = (j < k && c < kq) ? Cg[j * kq + c] : T(0);
+        __syncthreads();
+        for (int e = tid; e < KMAX * QMAX; e += blockDim.x) {
+            const int aa = e / QMAX, c = e % QMAX;
+            Cs[e] = (aa < k && c < kq) ? Cg[aa * kq + c] : T(0);
+        }
+        __syncthreads();
         T* out = (T*)P.U;
         const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
-        // RU rows per thread per iteration, all loads issued before the math, so
-        // that enough bytes are in flight to cover HBM latency
-        constexpr int RU = 4;
-        const int step = 8 * rows_per_warp;
-        for (int r0 = br.lo + warp * rows_per_warp + sub; r0 < br.hi; r0 += RU * step) {
-            T acc[RU];
+        const bool vec = (sizeof(T) == 4) && (k % 4 == 0) && (kout % 4 == 0) && (P.ldu % 4 == 0) &&
+                         ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+        for (int r0 = br.lo + tid; r0 < br.hi; r0 += RU * blockDim.x) {
+            T u[RU][KMAX];
 #pragma unroll
-            for (int u = 0; u < RU; ++u) acc[u] = T(0);
-            if (vec) {
+            for (int x = 0; x < RU; ++x) {
+                const int r = r0 + x * blockDim.x;
+                const T* ur = U + (int64_t)r * k;
+                if (vec) {
 #pragma unroll
-                for (int j = 0; j < KMAX; j += 4) {
-                    if (j >= k) break;
-                    float4 u4[RU];
-#pragma unroll
-                    for (int u = 0; u < RU; ++u) {
-                        const int r = r0 + u * step;
-                        u4[u] = (r < br.hi) ? __ldg(reinterpret_cast<const float4*>(U + (int64_t)r * k + j))
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int j = 0; j < KMAX; j += 4) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (j < k && r < br.hi) v = __ldg(reinterpret_cast<const float4*>(ur + j));
+                        u[x][j] = v.x; u[x][j + 1] = v.y; u[x][j + 2] = v.z; u[x][j + 3] = v.w;
                     }
+                } else {
 #pragma unroll
-                    for (int u = 0; u < RU; ++u)
-                        acc[u] += (T)u4[u].x * cc[j] + (T)u4[u].y * cc[j + 1] + (T)u4[u].z * cc[j + 2] +
-                                  (T)u4[u].w * cc[j + 3];
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < RU; ++u) {
-                    const int r = r0 + u * step;
-                    if (r >= br.hi) break;
-                    const T* ur = U + (int64_t)r * k;
-#pragma unroll
-                    for (int j = 0; j < KMAX; ++j) {
-                        if (j >= k) break;
-                        acc[u] += ur[j] * cc[j];
-                    }
+                    for (int j = 0; j < KMAX; ++j) u[x][j] = (j < k && r < br.hi) ? ur[j] : T(0);
                 }
             }
-            if (c < kout) {
 #pragma unroll
-                for (int u = 0; u < RU; ++u) {
-                    const int r = r0 + u * step;
-                    if (r < br.hi) out[(o0 + r) * P.ldu + c] = acc[u];
+            for (int x = 0; x < RU; ++x) {
+                const int r = r0 + x * blockDim.x;
+                if (r >= br.hi) break;
+                T acc[QMAX];
+#pragma unroll
+                for (int c = 0; c < QMAX; ++c) acc[c] = T(0);
+#pragma unroll
+                for (int j = 0; j < KMAX; ++j) {
+                    if (j >= k) break;
+                    const T uj = u[x][j];
+#pragma unroll
+                    for (int c = 0; c < QMAX; ++c) acc[c] += uj * Cs[j * QMAX + c];
+                }
+                T* orow = out + (o0 + r) * P.ldu;
+                if (vec) {
+#pragma unroll
+                    for (int c = 0; c < QMAX; c += 4) {
+                        if (c >= kout) break;
+                        *reinterpret_cast<float4*>(orow + c) = make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < QMAX; ++c)
+                        if (c < kout) orow[c] = acc[c];
                 }
             }
         }
@@ -1146,16 +1153,21 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
                : compress_impl<float, float, false>(c, tu, num_sms, st);
 }
 
+template <typename T, int KMAX>
+static void lift_q(const QueryArgs& a, int grid, cudaStream_t st) {
+    // the output width k_out (zero columns past k_q included) selects QMAX
+    if (a.kout <= 16) k_lift<T, KMAX, 16><<<grid, 256, 0, st>>>(a);
+    else if (a.kout <= 32) k_lift<T, KMAX, 32><<<grid, 256, 0, st>>>(a);
+    else k_lift<T, KMAX, 64><<<grid, 128, 0, st>>>(a);
+}
+
 template <typename T>
 static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int pers, cudaStream_t st) {
-    int grp = 1;
-    while (grp < a.kout) grp <<= 1;               // lanes per output row
-    if (grp > 32) return cudaErrorInvalidValue;
     prof::Scope ps("lift", st);
     const int grid = (int)std::min<int64_t>(max_slabs, pers);
-    if (a.k <= 16) k_lift<T, 16><<<grid, 256, 0, st>>>(a, grp);
-    else if (a.k <= 32) k_lift<T, 32><<<grid, 256, 0, st>>>(a, grp);
-    else k_lift<T, 64><<<grid, 256, 0, st>>>(a, grp);
+    if (a.k <= 16) lift_q<T, 16>(a, grid, st);
+    else if (a.k <= 32) lift_q<T, 32>(a, grid, st);
+    else lift_q<T, 64>(a, grid, st);
     return cudaGetLastError();
 }
 
