@@ -854,40 +854,42 @@ __global__ void __launch_bounds__(256) k_ur(QueryArgs a) {
 }
 
 // Lift (Eq. 9): output rows of each slab = U_i(rows) C_slab, zero past k_q.
-// One output row per lane: the lane reads its row of U_i (contiguous, vector
-// loads), multiplies by C_slab held in shared memory (read as warp-wide
-// broadcasts) and writes its contiguous output row; RU rows per lane are in
-// flight at once.
+// One warp per slab, one output row per lane: the warp keeps C_slab in its own
+// shared-memory slice (read as warp-wide broadcasts), each lane reads its row
+// of U_i (contiguous, vector loads) and writes its contiguous output row; RU
+// rows per lane are in flight at once.  No CTA barrier: while one warp loads
+// its next slab's coefficients the others stream rows.
 template <typename T, int KMAX, int QMAX>
 __global__ void __launch_bounds__(256) k_lift(QueryArgs a) {
-    __shared__ __align__(16) T Cs[KMAX * QMAX];
+    extern __shared__ __align__(16) char dsm[];
     const int k = a.k, kq = a.kq, kout = a.kout;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    T* Cs = (T*)dsm + (size_t)warp * KMAX * QMAX;
     const int nq = a.hdr->nq;
     const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
-    constexpr int RU = 2;
-    for (int64_t s = blockIdx.x; s < total; s += gridDim.x) {
+    constexpr int RU = KMAX >= 64 ? 1 : (KMAX >= 32 ? 2 : 4);   // register budget
+    for (int64_t s = (int64_t)blockIdx.x * wpc + warp; s < total; s += (int64_t)gridDim.x * wpc) {
         const int q = find_query(a.slab_prefix, nq, s);
         const QPlan& P = a.plans[q];
         const int t = (int)(s - P.slab0);
         const BlockRange br = slab_rows(P, t, a.b, Trows);
         const T* U = (const T*)a.U + (int64_t)br.blk * a.b * k;
         const T* Cg = (const T*)a.C + s * k * kq;
-        __syncthreads();
-        for (int e = tid; e < KMAX * QMAX; e += blockDim.x) {
+        __syncwarp();
+        for (int e = lane; e < KMAX * QMAX; e += 32) {
             const int aa = e / QMAX, c = e % QMAX;
             Cs[e] = (aa < k && c < kq) ? Cg[aa * kq + c] : T(0);
         }
-        __syncthreads();
+        __syncwarp();
         T* out = (T*)P.U;
         const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
         const bool vec = (sizeof(T) == 4) && (k % 4 == 0) && (kout % 4 == 0) && (P.ldu % 4 == 0) &&
                          ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
-        for (int r0 = br.lo + tid; r0 < br.hi; r0 += RU * blockDim.x) {
+        for (int r0 = br.lo + lane; r0 < br.hi; r0 += RU * 32) {
             T u[RU][KMAX];
 #pragma unroll
             for (int x = 0; x < RU; ++x) {
-                const int r = r0 + x * blockDim.x;
+                const int r = r0 + x * 32;
                 const T* ur = U + (int64_t)r * k;
                 if (vec) {
 #pragma unroll
@@ -903,7 +905,7 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a) {
             }
 #pragma unroll
             for (int x = 0; x < RU; ++x) {
-                const int r = r0 + x * blockDim.x;
+                const int r = r0 + x * 32;
                 if (r >= br.hi) break;
                 T acc[QMAX];
 #pragma unroll
@@ -1153,21 +1155,30 @@ cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const 
                : compress_impl<float, float, false>(c, tu, num_sms, st);
 }
 
+template <typename T, int KMAX, int QMAX>
+static void lift_launch(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
+    const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
+    const int wpc = threads / 32;
+    const size_t sm = sizeof(T) * (size_t)KMAX * QMAX * wpc;
+    set_smem(k_lift<T, KMAX, QMAX>, sm);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
+    k_lift<T, KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+}
+
 template <typename T, int KMAX>
-static void lift_q(const QueryArgs& a, int grid, cudaStream_t st) {
+static void lift_q(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
     // the output width k_out (zero columns past k_q included) selects QMAX
-    if (a.kout <= 16) k_lift<T, KMAX, 16><<<grid, 256, 0, st>>>(a);
-    else if (a.kout <= 32) k_lift<T, KMAX, 32><<<grid, 256, 0, st>>>(a);
-    else k_lift<T, KMAX, 64><<<grid, 128, 0, st>>>(a);
+    if (a.kout <= 16) lift_launch<T, KMAX, 16>(a, max_slabs, num_sms, st);
+    else if (a.kout <= 32) lift_launch<T, KMAX, 32>(a, max_slabs, num_sms, st);
+    else lift_launch<T, KMAX, 64>(a, max_slabs, num_sms, st);
 }
 
 template <typename T>
-static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int pers, cudaStream_t st) {
+static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
     prof::Scope ps("lift", st);
-    const int grid = (int)std::min<int64_t>(max_slabs, pers);
-    if (a.k <= 16) lift_q<T, 16>(a, grid, st);
-    else if (a.k <= 32) lift_q<T, 32>(a, grid, st);
-    else lift_q<T, 64>(a, grid, st);
+    if (a.k <= 16) lift_q<T, 16>(a, max_slabs, num_sms, st);
+    else if (a.k <= 32) lift_q<T, 32>(a, max_slabs, num_sms, st);
+    else lift_q<T, 64>(a, max_slabs, num_sms, st);
     return cudaGetLastError();
 }
 
@@ -1218,7 +1229,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
                 ZS_TRY(cudaGetLastError());
             }
             {
-                ZS_TRY(launch_lift<T>(a, max_slabs, pers, st));
+                ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
             }
             note_launches(4);
             return cudaSuccess;
@@ -1254,7 +1265,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
-    ZS_TRY(launch_lift<T>(a, max_slabs, pers, st));
+    ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
     note_launches(6);
     return cudaSuccess;
 }

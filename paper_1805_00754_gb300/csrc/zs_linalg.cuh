@@ -231,7 +231,17 @@ __device__ void mgs_orth(T* Q, int ldq, int n, int m, T* red, T* coef) {
 // work on different problems without CTA barriers.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int warp_jacobi(T* A, int lda, T* Z, int ldz, int m, int max_sweeps, bool init_z) {
+struct WarpRot {
+    int p[ZS_MAXM / 2], q[ZS_MAXM / 2];
+    T c[ZS_MAXM / 2], s[ZS_MAXM / 2];
+};
+
+// Cyclic Jacobi for one warp: lanes < m/2 compute the rotations of a
+// round-robin step and publish them in `wr` (shared memory); then every lane
+// applies all of them to its own column (row phase) and to its own row of A
+// and Z (column phase).  The pair updates are independent, so they pipeline.
+template <typename T>
+__device__ int warp_jacobi(T* A, int lda, T* Z, int ldz, int m, int max_sweeps, bool init_z, WarpRot<T>& wr) {
     const int lane = threadIdx.x & 31;
     if (init_z)
         for (int e = lane; e < m * m; e += 32) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
@@ -248,10 +258,9 @@ __device__ int warp_jacobi(T* A, int lda, T* Z, int ldz, int m, int max_sweeps, 
     for (; sweep < max_sweeps; ++sweep) {
         int rotated = 0;
         for (int r = 0; r < mm - 1; ++r) {
-            // pair of this lane (np <= 32 pairs for m <= 64)
-            int p = 0, q = 0;
-            T c = 1, s = 0;
+            T c = 1, sn = 0;
             if (lane < np) {
+                int p, q;
                 rr_pair(mm, r, lane, p, q);
                 if (q < m) {
                     const T apq = A[p * lda + q], app = A[p * lda + p], aqq = A[q * lda + q];
@@ -260,32 +269,40 @@ __device__ int warp_jacobi(T* A, int lda, T* Z, int ldz, int m, int max_sweeps, 
                         const T tau = (aqq - app) / (T(2) * apq);
                         const T t = (tau >= T(0) ? T(1) : T(-1)) / (zabs(tau) + zsqrt(T(1) + tau * tau));
                         c = T(1) / zsqrt(T(1) + t * t);
-                        s = t * c;
+                        sn = t * c;
                     }
+                } else {
+                    q = p;      // dummy index of an odd m: never rotated
                 }
+                wr.p[lane] = p;
+                wr.q[lane] = q;
+                wr.c[lane] = c;
+                wr.s[lane] = sn;
             }
-            rotated |= __any_sync(0xffffffffu, s != T(0));
+            rotated |= __any_sync(0xffffffffu, sn != T(0));
             __syncwarp();
-            // rows: A <- J^T A ; pair i handled via shuffles of (p, q, c, s)
-            for (int i = 0; i < np; ++i) {
-                const T si = __shfl_sync(0xffffffffu, s, i);
-                if (si == T(0)) continue;
-                const T ci = __shfl_sync(0xffffffffu, c, i);
-                const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
-                for (int j = lane; j < m; j += 32) {
+            // rows: A <- J^T A, lane owns column j
+            for (int j = lane; j < m; j += 32) {
+#pragma unroll 4
+                for (int i = 0; i < np; ++i) {
+                    const T si = wr.s[i];
+                    if (si == T(0)) continue;
+                    const T ci = wr.c[i];
+                    const int pi = wr.p[i], qi = wr.q[i];
                     const T ap = A[pi * lda + j], aq = A[qi * lda + j];
                     A[pi * lda + j] = ci * ap - si * aq;
                     A[qi * lda + j] = si * ap + ci * aq;
                 }
             }
             __syncwarp();
-            // columns: A <- A J, Z <- Z J
-            for (int i = 0; i < np; ++i) {
-                const T si = __shfl_sync(0xffffffffu, s, i);
-                if (si == T(0)) continue;
-                const T ci = __shfl_sync(0xffffffffu, c, i);
-                const int pi = __shfl_sync(0xffffffffu, p, i), qi = __shfl_sync(0xffffffffu, q, i);
-                for (int row = lane; row < m; row += 32) {
+            // columns: A <- A J and Z <- Z J, lane owns row `row`
+            for (int row = lane; row < m; row += 32) {
+#pragma unroll 4
+                for (int i = 0; i < np; ++i) {
+                    const T si = wr.s[i];
+                    if (si == T(0)) continue;
+                    const T ci = wr.c[i];
+                    const int pi = wr.p[i], qi = wr.q[i];
                     const T ap = A[row * lda + pi], aq = A[row * lda + qi];
                     A[row * lda + pi] = ci * ap - si * aq;
                     A[row * lda + qi] = si * ap + ci * aq;

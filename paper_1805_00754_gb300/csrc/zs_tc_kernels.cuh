@@ -46,6 +46,17 @@ struct SrcCompress {
         return (const char*)c.A + (size_t)j * c.b * c.lda * elem;
     }
     __device__ __forceinline__ int64_t ybase(int j) const { return (int64_t)j * c.b; }   // Y row offset
+    // row r of item j and the factor its values are scaled by; `Ctx` holds
+    // what is fixed per item (loaded once, outside the row loops)
+    struct Ctx { const char* base; };
+    __device__ __forceinline__ Ctx ctx(int j, int elem) const {
+        return Ctx{(const char*)c.A + (size_t)j * c.b * c.lda * elem};
+    }
+    template <typename Tin>
+    __device__ __forceinline__ const Tin* row(const Ctx& x, int r, float& scale) const {
+        scale = 1.f;
+        return (const Tin*)x.base + (size_t)r * c.lda;
+    }
     __device__ __forceinline__ int64_t tile0(int j) const { return (int64_t)j * ((c.b + 127) / 128); }
     __device__ __forceinline__ int64_t ntiles() const { return (int64_t)c.nblk * ((c.b + 127) / 128); }
     __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
@@ -64,6 +75,17 @@ struct SrcQuery {
         return (const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem;
     }
     __device__ __forceinline__ int64_t ybase(int q) const { return a.plans[q].slab0 * a.k; }
+    // row r of query q's stacked matrix M (Algorithm 2, stack step; written by
+    // the Partial-SVD and stack kernels)
+    struct Ctx { const char* base; };
+    __device__ __forceinline__ Ctx ctx(int q, int elem) const {
+        return Ctx{(const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem};
+    }
+    template <typename Tin>
+    __device__ __forceinline__ const Tin* row(const Ctx& x, int r, float& scale) const {
+        scale = 1.f;
+        return (const Tin*)x.base + (size_t)r * a.n;
+    }
     __device__ __forceinline__ int64_t tile0(int q) const { return a.plans[q].pad0; }
     __device__ __forceinline__ int64_t ntiles() const { return a.hdr->ntiles_total; }
     __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
@@ -119,6 +141,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
     for (int item = blockIdx.y; item < src.count(); item += gridDim.y) {
         const Tin* X = (const Tin*)src.X(item, sizeof(Tin));
         const bool xal = vec && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        const auto cx = src.ctx(item, sizeof(Tin));
         const int rows = src.rows(item);
         float acc[4][4][4];
 #pragma unroll
@@ -143,20 +166,21 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
                     float* v = pre[pnl][g];
                     v[0] = v[1] = v[2] = v[3] = 0.f;
                     if (gr < rows) {
-                        const Tin* src_p = X + (int64_t)gr * ld + gc;
+                        float sc = 1.f;
+                        const Tin* src_p = src.template row<Tin>(cx, gr, sc) + gc;
                         if constexpr (std::is_same<Tin, float>::value) {
                             if (xal && gc + 3 < n) {
                                 const float4 q = ld4<float>(src_p);
-                                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                                v[0] = q.x * sc; v[1] = q.y * sc; v[2] = q.z * sc; v[3] = q.w * sc;
                             } else {
 #pragma unroll
                                 for (int e = 0; e < 4; ++e)
-                                    if (gc + e < n) v[e] = (float)src_p[e];
+                                    if (gc + e < n) v[e] = (float)src_p[e] * sc;
                             }
                         } else {
 #pragma unroll
                             for (int e = 0; e < 4; ++e)
-                                if (gc + e < n) v[e] = __bfloat162float(src_p[e]);
+                                if (gc + e < n) v[e] = __bfloat162float(src_p[e]) * sc;
                         }
                     }
                 }
@@ -352,8 +376,9 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
         // each thread stages 8 groups of 4 consecutive values per 128 x 64 chunk;
         // the next chunk's loads are issued before the current chunk's MMAs
-        const bool xal = std::is_same<Tin, float>::value && (ld % 4 == 0) &&
+        const bool xal = std::is_same<Tin, float>::value && (ld % 4 == 0) && (n % 4 == 0) &&
                          ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        const auto cx = src.ctx(item, sizeof(Tin));
         float pre[8][4];
         auto fetch = [&](int k0) {
 #pragma unroll
@@ -363,20 +388,21 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
                 float* v = pre[g];
                 v[0] = v[1] = v[2] = v[3] = 0.f;
                 if (r0 + r < rows) {
-                    const Tin* p = X + (int64_t)(r0 + r) * ld + k0 + c;
+                    float sc = 1.f;
+                    const Tin* p = src.template row<Tin>(cx, r0 + r, sc) + k0 + c;
                     if constexpr (std::is_same<Tin, float>::value) {
                         if (xal && k0 + c + 3 < n) {
                             const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-                            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+                            v[0] = q.x * sc; v[1] = q.y * sc; v[2] = q.z * sc; v[3] = q.w * sc;
                         } else {
 #pragma unroll
                             for (int e = 0; e < 4; ++e)
-                                if (k0 + c + e < n) v[e] = __ldg(p + e);
+                                if (k0 + c + e < n) v[e] = __ldg(p + e) * sc;
                         }
                     } else {
 #pragma unroll
                         for (int e = 0; e < 4; ++e)
-                            if (k0 + c + e < n) v[e] = __bfloat162float(p[e]);
+                            if (k0 + c + e < n) v[e] = __bfloat162float(p[e]) * sc;
                     }
                 }
             }
@@ -475,7 +501,8 @@ __host__ __device__ __forceinline__ size_t rr_warp_bytes(int m) {
     const size_t ld = m + 1;
     const size_t tr = REF ? 8 : 4;
     // Hs, Cs(L), Li in TR; A_T, Z_T in float; REF: X, W in double
-    size_t b = 3 * tr * m * ld + 2 * 4 * m * ld + (REF ? 2 * 8 * m * ld : 0) + 4 * 64 + 8 * 64;
+    size_t b = 3 * tr * m * ld + 2 * 4 * m * ld + (REF ? 2 * 8 * m * ld : 0) + 4 * 64 + 8 * 64 +
+               sizeof(WarpRot<float>) + sizeof(WarpRot<double>) + 32;
     return (b + 15) & ~size_t(15);
 }
 
@@ -495,6 +522,10 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
     double* W = X + (REF ? (size_t)m * ld : 0);
     int* perm = (int*)(base + rr_warp_bytes<REF>(m) - 4 * 64 - 8 * 64);
     double* thd = (double*)(base + rr_warp_bytes<REF>(m) - 8 * 64);
+    char* rot = (char*)(X + (REF ? 2 * (size_t)m * ld : 0));
+    rot = (char*)(((uintptr_t)rot + 15) & ~(uintptr_t)15);
+    WarpRot<float>& wrf = *reinterpret_cast<WarpRot<float>*>(rot);
+    WarpRot<double>& wrd = *reinterpret_cast<WarpRot<double>*>(rot + ((sizeof(WarpRot<float>) + 15) & ~size_t(15)));
     const int count = src.count();
     for (int item = blockIdx.x * wpc + warp; item < count; item += gridDim.x * wpc) {
         const int rows = src.rows(item);
@@ -553,7 +584,7 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
             if (REF) X[i * ld + c] = (double)v;
         }
         __syncwarp();
-        warp_jacobi<float>(A_T, ld, Z_T, ld, m, 30, true);
+        warp_jacobi<float>(A_T, ld, Z_T, ld, m, 30, true, wrf);
         const double* Zsrc_d = nullptr;
         if constexpr (REF) {
             // B = Z^T H' Z in FP64 (X holds H'), then FP64 Jacobi (refinement)
@@ -572,7 +603,7 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
                 X[a * ld + c] = d;                        // B
             }
             __syncwarp();
-            warp_jacobi<double>(X, ld, W, ld, m, 4, true);
+            warp_jacobi<double>(X, ld, W, ld, m, 4, true, wrd);
             for (int e = lane; e < m * m; e += 32) {
                 const int i = e / m, c = e % m;
                 double d = 0;
