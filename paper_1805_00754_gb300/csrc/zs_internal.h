@@ -1,4 +1,4 @@
-// zs_internal.h - structures shared by the kernels (zs_kernels.cu) and the host
+// zs_internal.h - structures shared by the kernels (zs_kernels_dev.cuh) and the host
 // runtime (zs_api.cu, zs_serve.cpp).  Not part of the public ABI.
 #pragma once
 
@@ -125,7 +125,7 @@ inline int tc_width(int kq, int extra) {
     return m > 64 ? 64 : m;
 }
 
-// Launchers (zs_kernels.cu).  All enqueue on `st` and return cudaError_t of the
+// Launchers (zs_launch_common.cu).  All enqueue on `st` and return cudaError_t of the
 // launch.  `fp64` selects the double-precision instantiation (F64 store).
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu,
                             int num_sms, cudaStream_t st);

@@ -1,4 +1,4 @@
-// zs_kernels.cu - sm_103a kernels of the range-SVD hot path.
+// zs_kernels_dev.cuh - sm_103a device kernels of the range-SVD hot path.
 //
 // Storage phase (Section 3.2, Algorithm 1; one launch set per chunk of blocks):
 //   k_gram_compress   G_i = A_i^T A_i for every block (symmetric tiles)
@@ -11,99 +11,19 @@
 //   k_eig_query       top-k_q eigenpairs -> Sigma_r, V_r (Algorithm 2)
 //   k_ur              U_r = M V_r Sigma_r^{-1} and the per-slab lift
 //                     coefficients (Partial-SVD slabs folded with their Sigma V~ Sigma~^-1)
-//   k_lift            U_{S:E} = diag(S:E) U_r block by block (Eq. 9)
+// The tensor-core kernels of the float path are in zs_tc_kernels.cuh (included
+// at the end).  Every launcher translation unit includes this header and
+// instantiates only the kernels it launches.
+#pragma once
+
 #include <cuda_bf16.h>
 
-#include <algorithm>
-#include <atomic>
-#include <mutex>
-#include <string>
 #include <type_traits>
-#include <vector>
 
 #include "zs_internal.h"
 #include "zs_linalg.cuh"
 
 namespace zs {
-
-static std::atomic<int64_t> g_launches{0};
-void note_launches(int64_t n) { g_launches += n; }
-int64_t launch_count_total() { return g_launches.load(); }
-
-// ---------------------------------------------------------------------------
-// Kernel profiler: CUDA events around each launch, on the launch stream.
-// ---------------------------------------------------------------------------
-namespace prof {
-struct Pending { int id; cudaEvent_t a, b; };
-struct Entry { std::string name; int64_t launches = 0; double ms = 0; };
-static std::atomic<int> g_on{0};
-static std::mutex g_mu;
-static std::vector<Pending> g_pending;
-static std::vector<Entry> g_table;
-static std::vector<cudaEvent_t> g_pool;
-
-static cudaEvent_t get_event() {
-    if (!g_pool.empty()) { cudaEvent_t e = g_pool.back(); g_pool.pop_back(); return e; }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-}
-static void drain_locked() {
-    for (auto& p : g_pending) {
-        cudaEventSynchronize(p.b);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, p.a, p.b);
-        g_table[p.id].launches += 1;
-        g_table[p.id].ms += ms;
-        g_pool.push_back(p.a);
-        g_pool.push_back(p.b);
-    }
-    g_pending.clear();
-}
-struct Scope {
-    int id = -1;
-    cudaEvent_t a = nullptr, b = nullptr;
-    cudaStream_t st;
-    Scope(const char* name, cudaStream_t s) : st(s) {
-        if (!g_on.load(std::memory_order_relaxed)) return;
-        std::lock_guard<std::mutex> lk(g_mu);
-        for (size_t i = 0; i < g_table.size(); ++i)
-            if (g_table[i].name == name) { id = (int)i; break; }
-        if (id < 0) { g_table.push_back(Entry{name}); id = (int)g_table.size() - 1; }
-        a = get_event();
-        b = get_event();
-        cudaEventRecord(a, st);
-    }
-    ~Scope() {
-        if (id < 0) return;
-        cudaEventRecord(b, st);
-        std::lock_guard<std::mutex> lk(g_mu);
-        g_pending.push_back(Pending{id, a, b});
-        if (g_pending.size() > 4096) drain_locked();
-    }
-};
-}  // namespace prof
-
-void profile_enable(int on) { prof::g_on.store(on); }
-void profile_reset() {
-    std::lock_guard<std::mutex> lk(prof::g_mu);
-    prof::drain_locked();
-    prof::g_table.clear();
-}
-int profile_count() {
-    std::lock_guard<std::mutex> lk(prof::g_mu);
-    prof::drain_locked();
-    return (int)prof::g_table.size();
-}
-bool profile_get(int i, const char** name, int64_t* launches, double* ms) {
-    std::lock_guard<std::mutex> lk(prof::g_mu);
-    prof::drain_locked();
-    if (i < 0 || i >= (int)prof::g_table.size()) return false;
-    if (name) *name = prof::g_table[i].name.c_str();
-    if (launches) *launches = prof::g_table[i].launches;
-    if (ms) *ms = prof::g_table[i].ms;
-    return true;
-}
 
 __device__ __forceinline__ double ld_in(const double* p) { return __ldg(p); }
 __device__ __forceinline__ float ld_in(const float* p) { return __ldg(p); }
@@ -937,346 +857,3 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a) {
 }  // namespace zs
 
 #include "zs_tc_kernels.cuh"
-
-namespace zs {
-
-// ---------------------------------------------------------------------------
-// Host launchers.
-// ---------------------------------------------------------------------------
-size_t eig_smem_bytes(int n, int m, bool fp64, bool refine, bool yglob) {
-    const size_t ts = fp64 ? 8 : 4;
-    const bool dense = (m == n && n <= 64);
-    const size_t ld = m + 1;
-    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-    size_t s = 0;
-    if (!dense) s += (yglob ? 1 : 2) * r16(ts * n * ld);
-    s += 2 * r16(ts * m * ld);
-    if (refine && !fp64) s += 3 * r16(8 * m * ld);
-    return s;
-}
-
-// Subspace width m = kq + p (p = extra, at most 64 columns); the Y block moves
-// to global memory when shared memory cannot hold both n x m blocks.
-EigPlan eig_plan(int n, int kq, int extra, bool fp64, bool refine) {
-    EigPlan p;
-    const bool ref = refine && !fp64;
-    const size_t cap = 200 * 1024;
-    if (n <= 64) {
-        p.m = n;
-        p.yglob = false;
-        p.smem = eig_smem_bytes(n, n, fp64, ref, false);
-        p.ok = p.smem <= cap;
-        return p;
-    }
-    int m = std::min(std::min(n, kq + extra), ZS_MAXM);
-    if (eig_smem_bytes(n, m, fp64, ref, false) <= cap) {
-        p.m = m;
-        p.yglob = false;
-    } else {
-        while (m > kq + 2 && eig_smem_bytes(n, m, fp64, ref, true) > cap) --m;
-        p.m = m;
-        p.yglob = true;
-    }
-    p.smem = eig_smem_bytes(n, p.m, fp64, ref, p.yglob);
-    p.ok = p.smem <= cap && p.m >= kq;
-    return p;
-}
-
-size_t eig_ws_bytes(int n, bool fp64, int ctas) {
-    return (size_t)(fp64 ? 8 : 4) * n * (ZS_MAXM + 1) * std::max(ctas, 1);
-}
-
-// Opt in to the dynamic shared memory a launch needs (static + dynamic may not
-// exceed 48 KB without it).
-template <typename K>
-static cudaError_t set_smem(K kern, size_t bytes) {
-    if (bytes <= 32 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-#define ZS_TRY(x)                                  \
-    do {                                           \
-        cudaError_t e_ = (x);                      \
-        if (e_ != cudaSuccess) return e_;          \
-    } while (0)
-
-template <typename Tin, typename T, bool REF>
-static cudaError_t compress_impl(const CompressChunk& c, const Tuning& tu, int num_sms, cudaStream_t st) {
-    const int ntile = (c.n + 63) / 64;
-    const int npairs = ntile * (ntile + 1) / 2;
-    dim3 gg(npairs, std::min(c.nblk, 65535));
-    {
-        prof::Scope ps("gram_compress", st);
-        k_gram_compress<Tin, T><<<gg, 256, 0, st>>>(c);
-    }
-    ZS_TRY(cudaGetLastError());
-    const bool fp64 = std::is_same<T, double>::value;
-    const EigPlan ep = eig_plan(c.n, c.k, tu.eig_m_extra, fp64, REF);
-    if (!ep.ok) return cudaErrorInvalidValue;
-    const int grid_e = std::min(c.nblk, ep.yglob ? c.ews_ctas : 65535);
-    if (ep.m <= 32) {
-        ZS_TRY(set_smem(k_eig_compress<T, REF, 32>, ep.smem));
-        prof::Scope ps("eig_compress", st);
-        k_eig_compress<T, REF, 32><<<grid_e, 256, ep.smem, st>>>(c, ep.m, ep.yglob, c.ews);
-    } else {
-        ZS_TRY(set_smem(k_eig_compress<T, REF, 64>, ep.smem));
-        prof::Scope ps("eig_compress", st);
-        k_eig_compress<T, REF, 64><<<grid_e, 256, ep.smem, st>>>(c, ep.m, ep.yglob, c.ews);
-    }
-    ZS_TRY(cudaGetLastError());
-    const size_t smu = sizeof(T) * ((size_t)c.k * (c.n + 1) + 32 * (size_t)(c.n + 1) + c.k) + 64;
-    ZS_TRY(set_smem(k_form_u<Tin, T>, smu));
-    dim3 gu(std::min((c.b + 31) / 32, 8), std::min(c.nblk, 65535));
-    {
-        prof::Scope ps("form_u", st);
-        k_form_u<Tin, T><<<gu, 256, smu, st>>>(c);
-    }
-    ZS_TRY(cudaGetLastError());
-    note_launches(3);
-    (void)num_sms;
-    return cudaSuccess;
-}
-
-// ---------------------------------------------------------------------------
-// Tensor-core path (see zs_tc_kernels.cuh).
-// ---------------------------------------------------------------------------
-static size_t tc_subspace_smem(int n, int m, bool& yglob) {
-    const size_t both = (size_t)2 * n * (m + 1) * 4;
-    yglob = both > 110 * 1024;
-    return yglob ? (size_t)n * (m + 1) * 4 : both;
-}
-static size_t tc_project_smem(int n, int m) {
-    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)3 * 128 * 72 * 2;
-}
-
-// Auxiliary scratch of the tensor path, carved from one buffer:
-// [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw]
-size_t tc_aux_bytes(int64_t items, int64_t tiles, int m, int kw) {
-    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return r(4 * (size_t)tiles * m * m) + r(4 * (size_t)items * m * m) + r(4 * (size_t)items * m * kw) +
-           r(4 * (size_t)items * kw);
-}
-static void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, int kw, TcScratch& sc) {
-    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
-    char* p = (char*)aux;
-    sc.Hp = (float*)p;
-    p += r(4 * (size_t)tiles * m * m);
-    sc.Cq = (float*)p;
-    p += r(4 * (size_t)items * m * m);
-    sc.Zs = (float*)p;
-    p += r(4 * (size_t)items * m * kw);
-    sc.th = (float*)p;
-}
-
-template <class Src, typename Tin, bool REF, bool QUERY>
-static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
-                           int ews_ctas, int num_sms, int proj_per_sm, cudaStream_t st) {
-    const int ntile = (n + 127) / 128;
-    const int npairs = ntile * (ntile + 1) / 2;
-    const int gi = std::min(max_items, 65535);
-    {
-        prof::Scope ps(QUERY ? "gram_lo_query" : "gram_lo", st);
-        k_gram_lo<Src, Tin><<<dim3(npairs, gi), 256, 0, st>>>(src, sc, n);
-    }
-    ZS_TRY(cudaGetLastError());
-    {
-        bool yglob;
-        const size_t sm = tc_subspace_smem(n, sc.m, yglob);
-        const int gs = std::min(gi, yglob ? ews_ctas : 65535);
-        prof::Scope ps(QUERY ? "subspace_query" : "subspace", st);
-        if (sc.m <= 32) {
-            ZS_TRY(set_smem(k_subspace<Src, 32>, sm));
-            k_subspace<Src, 32><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
-        } else {
-            ZS_TRY(set_smem(k_subspace<Src, 64>, sm));
-            k_subspace<Src, 64><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
-        }
-    }
-    ZS_TRY(cudaGetLastError());
-    {
-        const size_t sm = tc_project_smem(n, sc.m);
-        ZS_TRY(set_smem(k_project<Src, Tin>, sm));
-        prof::Scope ps(QUERY ? "project_query" : "project", st);
-        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * proj_per_sm);
-        k_project<Src, Tin><<<std::max(gp, 1), 256, sm, st>>>(src, sc, n);
-    }
-    ZS_TRY(cudaGetLastError());
-    {
-        const size_t per = rr_warp_bytes<REF>(sc.m);
-        const int wpc = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / per));
-        const size_t sm = per * wpc;
-        ZS_TRY(set_smem(k_rr_core<Src, REF>, sm));
-        prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
-        k_rr_core<Src, REF><<<std::min((max_items + wpc - 1) / wpc, 65535), 32 * wpc, sm, st>>>(src, sc, kw);
-    }
-    ZS_TRY(cudaGetLastError());
-    {
-        const size_t sm = sizeof(float) * ((size_t)sc.m * kw + (size_t)n * kw);
-        ZS_TRY(set_smem(k_rr_out<Src, QUERY>, sm));
-        prof::Scope ps(QUERY ? "rr_out_query" : "rr_out", st);
-        k_rr_out<Src, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
-    }
-    ZS_TRY(cudaGetLastError());
-    note_launches(5);
-    return cudaSuccess;
-}
-
-template <typename Tin, bool REF>
-static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num_sms, cudaStream_t st) {
-    TcScratch sc;
-    sc.G = (float*)c.G;
-    sc.Qb = (__nv_bfloat16*)c.qb;
-    sc.Y = (float*)c.ys;
-    sc.ews = c.ews;
-    sc.ews_ctas = std::max(1, c.ews_ctas);
-    sc.m = tc_width(c.k, tu.eig_m_extra);
-    sc.power_its = tu.power_its;
-    tc_aux_carve(c.aux, c.nblk, (int64_t)c.nblk * ((c.b + 127) / 128), sc.m, c.k, sc);
-    SrcCompress src{c};
-    return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,
-                                                 (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms,
-                                                 tu.project_ctas_per_sm, st);
-}
-
-cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
-                            cudaStream_t st) {
-    const bool ref = (flags & 1) != 0;
-    if (use_tc_path(fp64, c.n, flags)) {
-        if (c.in_kind == IN_BF16)
-            return ref ? compress_tc<__nv_bfloat16, true>(c, tu, num_sms, st)
-                       : compress_tc<__nv_bfloat16, false>(c, tu, num_sms, st);
-        return ref ? compress_tc<float, true>(c, tu, num_sms, st) : compress_tc<float, false>(c, tu, num_sms, st);
-    }
-    if (fp64) return compress_impl<double, double, false>(c, tu, num_sms, st);
-    if (c.in_kind == IN_BF16)
-        return ref ? compress_impl<__nv_bfloat16, float, true>(c, tu, num_sms, st)
-                   : compress_impl<__nv_bfloat16, float, false>(c, tu, num_sms, st);
-    return ref ? compress_impl<float, float, true>(c, tu, num_sms, st)
-               : compress_impl<float, float, false>(c, tu, num_sms, st);
-}
-
-template <typename T, int KMAX, int QMAX>
-static void lift_launch(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
-    const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
-    const int wpc = threads / 32;
-    const size_t sm = sizeof(T) * (size_t)KMAX * QMAX * wpc;
-    set_smem(k_lift<T, KMAX, QMAX>, sm);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
-    k_lift<T, KMAX, QMAX><<<grid, threads, sm, st>>>(a);
-}
-
-template <typename T, int KMAX>
-static void lift_q(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
-    // the output width k_out (zero columns past k_q included) selects QMAX
-    if (a.kout <= 16) lift_launch<T, KMAX, 16>(a, max_slabs, num_sms, st);
-    else if (a.kout <= 32) lift_launch<T, KMAX, 32>(a, max_slabs, num_sms, st);
-    else lift_launch<T, KMAX, 64>(a, max_slabs, num_sms, st);
-}
-
-template <typename T>
-static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
-    prof::Scope ps("lift", st);
-    if (a.k <= 16) lift_q<T, 16>(a, max_slabs, num_sms, st);
-    else if (a.k <= 32) lift_q<T, 32>(a, max_slabs, num_sms, st);
-    else lift_q<T, 64>(a, max_slabs, num_sms, st);
-    return cudaGetLastError();
-}
-
-template <typename T, bool REF>
-static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu, int num_sms,
-                              cudaStream_t st) {
-    const int max_nq = g.nq;
-    const int64_t max_slabs = g.slabs;
-    const bool fp64 = std::is_same<T, double>::value;
-    const int k = a.k, n = a.n, kq = a.kq;
-    const int pers = std::max(1, num_sms * tu.slab_ctas_per_sm);
-    const bool tc = use_tc_path(fp64, n, flags);
-    // Partial-SVD
-    {
-        const int ld = k + 1;
-        auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
-        size_t sm = 2 * r16(sizeof(T) * k * ld) + r16(sizeof(T) * 64 * ld);
-        if (REF) sm += 3 * r16(sizeof(double) * k * ld);
-        ZS_TRY(set_smem(k_partial<T, REF>, sm));
-        prof::Scope ps("partial_svd", st);
-        k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
-        ZS_TRY(cudaGetLastError());
-    }
-    {
-        prof::Scope ps("stack", st);
-        k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
-    }
-    ZS_TRY(cudaGetLastError());
-    if constexpr (!std::is_same<T, double>::value) {
-        if (tc) {
-            TcScratch sc;
-            sc.G = (float*)a.G;
-            sc.Qb = (__nv_bfloat16*)a.qb;
-            sc.Y = (float*)a.ys;
-            sc.ews = a.ews;
-            sc.ews_ctas = std::max(1, a.ews_ctas);
-            sc.m = tc_width(kq, tu.eig_m_extra);
-            sc.power_its = tu.power_its;
-            tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
-            SrcQuery src{a};
-            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
-                                                        tu.project_ctas_per_sm, st)));
-            {
-                const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
-                ZS_TRY(set_smem(k_bfix, sm));
-                prof::Scope ps("boundary_fix", st);
-                k_bfix<<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
-                ZS_TRY(cudaGetLastError());
-            }
-            {
-                ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
-            }
-            note_launches(4);
-            return cudaSuccess;
-        }
-    }
-    {
-        const int ntile = (n + 63) / 64;
-        const int npairs = ntile * (ntile + 1) / 2;
-        dim3 gg(npairs, std::min(max_nq, 65535));
-        prof::Scope ps("gram_query", st);
-        k_gram_query<T><<<gg, 256, 0, st>>>(a);
-        ZS_TRY(cudaGetLastError());
-    }
-    {
-        const EigPlan ep = eig_plan(n, kq, tu.eig_m_extra, fp64, REF);
-        if (!ep.ok) return cudaErrorInvalidValue;
-        const int grid = std::min(max_nq, ep.yglob ? a.ews_ctas : 65535);
-        if (ep.m <= 32) {
-            ZS_TRY(set_smem(k_eig_query<T, REF, 32>, ep.smem));
-            prof::Scope ps("eig_query", st);
-            k_eig_query<T, REF, 32><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
-        } else {
-            ZS_TRY(set_smem(k_eig_query<T, REF, 64>, ep.smem));
-            prof::Scope ps("eig_query", st);
-            k_eig_query<T, REF, 64><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
-        }
-        ZS_TRY(cudaGetLastError());
-    }
-    {
-        const size_t sm = sizeof(T) * ((size_t)kq * (n + 1) + (size_t)k * (n + 1) + (size_t)k * kq + (size_t)k * k) + 64;
-        ZS_TRY(set_smem(k_ur<T>, sm));
-        prof::Scope ps("stitched_u", st);
-        k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
-        ZS_TRY(cudaGetLastError());
-    }
-    ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
-    note_launches(6);
-    return cudaSuccess;
-}
-
-cudaError_t launch_query(const QueryArgs& a, bool fp64, const QueryGrid& g, int flags, const Tuning& tu,
-                         int num_sms, cudaStream_t st) {
-    if (fp64) return query_impl<double, false>(a, g, flags, tu, num_sms, st);
-    return a.fp64_refine ? query_impl<float, true>(a, g, flags, tu, num_sms, st)
-                         : query_impl<float, false>(a, g, flags, tu, num_sms, st);
-}
-
-bool profiling_on() { return prof::g_on.load() != 0; }
-
-}  // namespace zs

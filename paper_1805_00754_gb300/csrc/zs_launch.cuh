@@ -1,0 +1,234 @@
+// zs_launch.cuh - host-side launch helpers shared by the launcher translation
+// units (zs_compress_*.cu, zs_query_*.cu): shared-memory opt-in, the
+// tensor-path scratch carving and launch sequence, and the query launch set.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "zs_kernels_dev.cuh"
+#include "zs_prof.h"
+
+namespace zs {
+
+// Opt in to the dynamic shared memory a launch needs (static + dynamic may not
+// exceed 48 KB without it).
+template <typename K>
+static cudaError_t set_smem(K kern, size_t bytes) {
+    if (bytes <= 32 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+#define ZS_TRY(x)                                  \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return e_;          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Tensor-core path (see zs_tc_kernels.cuh).
+// ---------------------------------------------------------------------------
+static inline size_t tc_subspace_smem(int n, int m, bool& yglob) {
+    const size_t both = (size_t)2 * n * (m + 1) * 4;
+    yglob = both > 110 * 1024;
+    return yglob ? (size_t)n * (m + 1) * 4 : both;
+}
+static inline size_t tc_project_smem(int n, int m) {
+    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)3 * 128 * 72 * 2;
+}
+
+// Auxiliary scratch of the tensor path, carved from one buffer:
+// [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw]
+
+static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, int kw, TcScratch& sc) {
+    auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+    char* p = (char*)aux;
+    sc.Hp = (float*)p;
+    p += r(4 * (size_t)tiles * m * m);
+    sc.Cq = (float*)p;
+    p += r(4 * (size_t)items * m * m);
+    sc.Zs = (float*)p;
+    p += r(4 * (size_t)items * m * kw);
+    sc.th = (float*)p;
+}
+
+template <class Src, typename Tin, bool REF, bool QUERY>
+static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
+                           int ews_ctas, int num_sms, int proj_per_sm, cudaStream_t st) {
+    const int ntile = (n + 127) / 128;
+    const int npairs = ntile * (ntile + 1) / 2;
+    const int gi = std::min(max_items, 65535);
+    {
+        prof::Scope ps(QUERY ? "gram_lo_query" : "gram_lo", st);
+        k_gram_lo<Src, Tin><<<dim3(npairs, gi), 256, 0, st>>>(src, sc, n);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        bool yglob;
+        const size_t sm = tc_subspace_smem(n, sc.m, yglob);
+        const int gs = std::min(gi, yglob ? ews_ctas : 65535);
+        prof::Scope ps(QUERY ? "subspace_query" : "subspace", st);
+        if (sc.m <= 32) {
+            ZS_TRY(set_smem(k_subspace<Src, 32>, sm));
+            k_subspace<Src, 32><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+        } else {
+            ZS_TRY(set_smem(k_subspace<Src, 64>, sm));
+            k_subspace<Src, 64><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
+        }
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        const size_t sm = tc_project_smem(n, sc.m);
+        ZS_TRY(set_smem(k_project<Src, Tin>, sm));
+        prof::Scope ps(QUERY ? "project_query" : "project", st);
+        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * proj_per_sm);
+        k_project<Src, Tin><<<std::max(gp, 1), 256, sm, st>>>(src, sc, n);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        const size_t per = rr_warp_bytes<REF>(sc.m);
+        const int wpc = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / per));
+        const size_t sm = per * wpc;
+        ZS_TRY(set_smem(k_rr_core<Src, REF>, sm));
+        prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
+        k_rr_core<Src, REF><<<std::min((max_items + wpc - 1) / wpc, 65535), 32 * wpc, sm, st>>>(src, sc, kw);
+    }
+    ZS_TRY(cudaGetLastError());
+    {
+        const size_t sm = sizeof(float) * ((size_t)sc.m * kw + (size_t)n * kw);
+        ZS_TRY(set_smem(k_rr_out<Src, QUERY>, sm));
+        prof::Scope ps(QUERY ? "rr_out_query" : "rr_out", st);
+        k_rr_out<Src, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
+    }
+    ZS_TRY(cudaGetLastError());
+    note_launches(5);
+    return cudaSuccess;
+}
+
+template <typename T, int KMAX, int QMAX>
+static void lift_launch(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
+    const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
+    const int wpc = threads / 32;
+    const size_t sm = sizeof(T) * (size_t)KMAX * QMAX * wpc;
+    set_smem(k_lift<T, KMAX, QMAX>, sm);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
+    k_lift<T, KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+}
+
+template <typename T, int KMAX>
+static void lift_q(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
+    // the output width k_out (zero columns past k_q included) selects QMAX
+    if (a.kout <= 16) lift_launch<T, KMAX, 16>(a, max_slabs, num_sms, st);
+    else if (a.kout <= 32) lift_launch<T, KMAX, 32>(a, max_slabs, num_sms, st);
+    else lift_launch<T, KMAX, 64>(a, max_slabs, num_sms, st);
+}
+
+template <typename T>
+static cudaError_t launch_lift(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
+    prof::Scope ps("lift", st);
+    if (a.k <= 16) lift_q<T, 16>(a, max_slabs, num_sms, st);
+    else if (a.k <= 32) lift_q<T, 32>(a, max_slabs, num_sms, st);
+    else lift_q<T, 64>(a, max_slabs, num_sms, st);
+    return cudaGetLastError();
+}
+
+template <typename T, bool REF>
+static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu, int num_sms,
+                              cudaStream_t st) {
+    const int max_nq = g.nq;
+    const int64_t max_slabs = g.slabs;
+    const bool fp64 = std::is_same<T, double>::value;
+    const int k = a.k, n = a.n, kq = a.kq;
+    const int pers = std::max(1, num_sms * tu.slab_ctas_per_sm);
+    const bool tc = use_tc_path(fp64, n, flags);
+    // Partial-SVD
+    {
+        const int ld = k + 1;
+        auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+        size_t sm = 2 * r16(sizeof(T) * k * ld) + r16(sizeof(T) * 64 * ld);
+        if (REF) sm += 3 * r16(sizeof(double) * k * ld);
+        ZS_TRY(set_smem(k_partial<T, REF>, sm));
+        prof::Scope ps("partial_svd", st);
+        k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        prof::Scope ps("stack", st);
+        k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
+    }
+    ZS_TRY(cudaGetLastError());
+    if constexpr (!std::is_same<T, double>::value) {
+        if (tc) {
+            TcScratch sc;
+            sc.G = (float*)a.G;
+            sc.Qb = (__nv_bfloat16*)a.qb;
+            sc.Y = (float*)a.ys;
+            sc.ews = a.ews;
+            sc.ews_ctas = std::max(1, a.ews_ctas);
+            sc.m = tc_width(kq, tu.eig_m_extra);
+            sc.power_its = tu.power_its;
+            tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
+            SrcQuery src{a};
+            ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
+                                                        tu.project_ctas_per_sm, st)));
+            {
+                const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
+                ZS_TRY(set_smem(k_bfix, sm));
+                prof::Scope ps("boundary_fix", st);
+                k_bfix<<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+                ZS_TRY(cudaGetLastError());
+            }
+            {
+                ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
+            }
+            note_launches(4);
+            return cudaSuccess;
+        }
+    }
+    {
+        const int ntile = (n + 63) / 64;
+        const int npairs = ntile * (ntile + 1) / 2;
+        dim3 gg(npairs, std::min(max_nq, 65535));
+        prof::Scope ps("gram_query", st);
+        k_gram_query<T><<<gg, 256, 0, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        const EigPlan ep = eig_plan(n, kq, tu.eig_m_extra, fp64, REF);
+        if (!ep.ok) return cudaErrorInvalidValue;
+        const int grid = std::min(max_nq, ep.yglob ? a.ews_ctas : 65535);
+        if (ep.m <= 32) {
+            ZS_TRY(set_smem(k_eig_query<T, REF, 32>, ep.smem));
+            prof::Scope ps("eig_query", st);
+            k_eig_query<T, REF, 32><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
+        } else {
+            ZS_TRY(set_smem(k_eig_query<T, REF, 64>, ep.smem));
+            prof::Scope ps("eig_query", st);
+            k_eig_query<T, REF, 64><<<grid, 256, ep.smem, st>>>(a, ep.m, ep.yglob, a.ews);
+        }
+        ZS_TRY(cudaGetLastError());
+    }
+    {
+        const size_t sm = sizeof(T) * ((size_t)kq * (n + 1) + (size_t)k * (n + 1) + (size_t)k * kq + (size_t)k * k) + 64;
+        ZS_TRY(set_smem(k_ur<T>, sm));
+        prof::Scope ps("stitched_u", st);
+        k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+    }
+    ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
+    note_launches(6);
+    return cudaSuccess;
+}
+
+// Per-precision query launchers (zs_query_f64.cu, zs_query_f32.cu, zs_query_f32r.cu).
+cudaError_t launch_query_f64(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_query_f32(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_query_f32_refine(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu,
+                                    int num_sms, cudaStream_t st);
+cudaError_t launch_compress_simt(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
+                                 cudaStream_t st);
+cudaError_t launch_compress_tc(const CompressChunk& c, int flags, const Tuning& tu, int num_sms, cudaStream_t st);
+
+}  // namespace zs

@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
 }
 
 // Query boundary slabs: C_slab <- (Sigma V~ Sigma~^{-1}) C_slab  (k x kq), in place.
-__global__ void __launch_bounds__(256) k_bfix(QueryArgs a) {
+static __global__ void __launch_bounds__(256) k_bfix(QueryArgs a) {
     extern __shared__ __align__(16) char dsm[];
     const int k = a.k, kq = a.kq;
     float* Tc = (float*)dsm;          // k x k
