@@ -114,7 +114,7 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
     if ((s = al(&ews, eig_ws_bytes((int)n, st.fp64, ews_ctas), "eigen workspace")) != ZS_OK) return s;
     if (use_tc_path(st.fp64, (int)n, st.cfg.flags)) {
         const size_t m = tc_width(want_kq, st.tune.eig_m_extra);
-        if ((s = al(&qb, 2 * m * (size_t)n * want_nq, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&qb, 4 * m * (size_t)n * want_nq, "subspace bases")) != ZS_OK) return s;
         if ((s = al(&ys, 4 * m * (size_t)want_sl * k, "projections")) != ZS_OK) return s;
         aux_tiles = (int64_t)want_sl * k / 128 + want_nq;
         if ((s = al(&aux, tc_aux_bytes(want_nq, aux_tiles, (int)m, want_kq), "Rayleigh-Ritz scratch")) != ZS_OK)
@@ -131,7 +131,7 @@ size_t QueryExec::bytes_for(const zs_store& st, int nq, int64_t nslab, int kq) {
     const size_t n = st.cfg.n, k = st.cfg.k;
     const size_t m = 64;
     return tc_aux_bytes(nq, (int64_t)nslab * k / 128 + nq, 64, kq) + ts * (nslab * k * n + (size_t)nq * n * n + (size_t)nq * kq * (n + 1) + 2 * (size_t)nq * k * k +
-                 nslab * k * kq + nslab * k * m + (size_t)nq * n * m / 2) + sizeof(QPlan) * nq;
+                 nslab * k * kq + nslab * k * m + (size_t)nq * n * m) + sizeof(QPlan) * nq;
 }
 
 // Drop the appends that have finished on the device.
@@ -311,13 +311,13 @@ static zs_status store_alloc(zs_store* st) {
     // Gram scratch: chunk of blocks whose n x n Grams stay L2-sized
     const size_t gper = ts * (size_t)c.n * c.n;
     const size_t mtc = use_tc_path(st->fp64, (int)c.n, c.flags) ? tc_width(c.k, st->tune.eig_m_extra) : 0;
-    const size_t per_block = gper + 2 * mtc * c.n + 4 * mtc * c.b +
+    const size_t per_block = gper + 4 * mtc * c.n + 4 * mtc * c.b +
                              (mtc ? 4 * mtc * mtc * ((c.b + 127) / 128 + 1) + 4 * mtc * c.k + 4 * c.k : 0);
     st->gchunk = (int)std::max<size_t>(1, std::min<size_t>(st->gram_budget / per_block, 65535));
     if ((s = al(&st->gscr, gper * st->gchunk, "gram scratch")) != ZS_OK) return s;
     if (use_tc_path(st->fp64, (int)c.n, c.flags)) {
         const size_t m = tc_width(c.k, st->tune.eig_m_extra);
-        if ((s = al(&st->qb, 2 * m * (size_t)c.n * st->gchunk, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&st->qb, 4 * m * (size_t)c.n * st->gchunk, "subspace bases")) != ZS_OK) return s;
         if ((s = al(&st->ys, 4 * m * (size_t)c.b * st->gchunk, "projections")) != ZS_OK) return s;
         if ((s = al(&st->aux, tc_aux_bytes(st->gchunk, (int64_t)st->gchunk * ((c.b + 127) / 128), (int)m, c.k),
                     "Rayleigh-Ritz scratch")) != ZS_OK)
@@ -339,7 +339,7 @@ static zs_status store_alloc(zs_store* st) {
             if ((s = al(&ps.G, gper, "append pipeline gram")) != ZS_OK) return s;
             if ((s = al(&ps.ews, eig_ws_bytes((int)c.n, st->fp64, 1), "append pipeline workspace")) != ZS_OK) return s;
             if (mt) {
-                if ((s = al(&ps.qb, 2 * mt * (size_t)c.n, "append pipeline bases")) != ZS_OK) return s;
+                if ((s = al(&ps.qb, 4 * mt * (size_t)c.n, "append pipeline bases")) != ZS_OK) return s;
                 if ((s = al(&ps.ys, 4 * mt * (size_t)c.b, "append pipeline projections")) != ZS_OK) return s;
                 if ((s = al(&ps.aux, tc_aux_bytes(1, (c.b + 127) / 128, (int)mt, c.k), "append pipeline RR")) != ZS_OK)
                     return s;

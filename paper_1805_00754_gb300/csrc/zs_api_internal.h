@@ -67,7 +67,7 @@ struct zs_store {
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace
     int ews_ctas = 1;
-    void* qb = nullptr;            // tensor path: subspace bases (gchunk x n x m bf16)
+    void* qb = nullptr;            // tensor path: subspace bases (gchunk x n x m, tf32 values)
     void* ys = nullptr;            // tensor path: projections (gchunk x b x m float)
     void* aux = nullptr;           // tensor path: Rayleigh-Ritz scratch
     int gchunk = 1;

@@ -9,7 +9,7 @@ template <typename Tin, bool REF>
 static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num_sms, cudaStream_t st) {
     TcScratch sc;
     sc.G = (float*)c.G;
-    sc.Qb = (__nv_bfloat16*)c.qb;
+    sc.Qf = (float*)c.qb;
     sc.Y = (float*)c.ys;
     sc.ews = c.ews;
     sc.ews_ctas = std::max(1, c.ews_ctas);
@@ -19,7 +19,7 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
     SrcCompress src{c};
     return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,
                                                  (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms,
-                                                 tu.project_ctas_per_sm, st);
+                                                 tu, st);
 }
 
 cudaError_t launch_compress_tc(const CompressChunk& c, int flags, const Tuning& tu, int num_sms, cudaStream_t st) {

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 namespace zs {
@@ -34,7 +36,7 @@ struct CompressChunk {
     void* vt;         // store: k * n per slot
     void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
     int32_t ews_ctas;
-    void* qb;         // tensor path: nblk x n x 64 bf16 subspace bases
+    void* qb;         // tensor path: nblk x n x m subspace bases (fp32 holding tf32 values)
     void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
     void* aux;        // tensor path: tc_aux_bytes(nblk, nblk*ceil(b/128), m, k)
 };
@@ -99,7 +101,7 @@ struct QueryArgs {
     void* C;          // nslab_total * k * kq    lift coefficients per slab
     void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
     int32_t ews_ctas;
-    void* qb;         // tensor path: nq x n x 64 bf16 subspace bases
+    void* qb;         // tensor path: nq x n x m subspace bases (fp32 holding tf32 values)
     void* ys;         // tensor path: nslab_total x k x 64 floats (Y = M Q~)
     void* aux;        // tensor path: tc_aux_bytes(nq, aux_tiles, m, kq)
     int64_t aux_tiles;
@@ -113,6 +115,7 @@ struct Tuning {
     int eig_m_extra = 16;        // subspace oversampling p (m = kq + p)
     int power_its = 1;           // tensor path: power steps on the bf16 Gram
     int project_ctas_per_sm = 8; // persistent grid of the projection kernel
+    int fused_sketch = 1;        // tensor path: sketch kernel (else the bf16 Gram) where it fits
 };
 
 // The tensor-core path (bf16 Gram for the subspace, split-bf16 projection and
@@ -120,8 +123,13 @@ struct Tuning {
 // subspace width m <= 64 must not exceed n) unless the store asks for the
 // exact FP32 Gram.
 inline bool use_tc_path(bool fp64, int n, int flags) { return !fp64 && n >= 64 && !(flags & 2); }
+// Subspace width m = kq + p rounded up to 8: the oversampling p is `extra`,
+// reduced (not below 8) where that keeps m <= 32, the width of the register
+// Rayleigh-Ritz core.
 inline int tc_width(int kq, int extra) {
-    int m = ((kq + extra) + 7) / 8 * 8;
+    int p = extra;
+    if (kq + p > 32) p = std::max(8, std::min(extra, 32 - kq));
+    int m = ((kq + p) + 7) / 8 * 8;
     return m > 64 ? 64 : m;
 }
 

@@ -33,9 +33,6 @@ static inline size_t tc_subspace_smem(int n, int m, bool& yglob) {
     yglob = both > 110 * 1024;
     return yglob ? (size_t)n * (m + 1) * 4 : both;
 }
-static inline size_t tc_project_smem(int n, int m) {
-    return (size_t)((n + 15) / 16 * 16) * bf16_ld(m) * 2 + (size_t)3 * 128 * 72 * 2;
-}
 
 // Auxiliary scratch of the tensor path, carved from one buffer:
 // [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw]
@@ -52,18 +49,55 @@ static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, 
     sc.th = (float*)p;
 }
 
+// The sketch kernel covers n <= 512 with its accumulator S (n x m) held in
+// registers: 16 NMT rows per warp, m <= MB.
+static inline bool sketch_fits(int n, int m) {
+    if (n > 512 || (n > 256 && m > 32)) return false;
+    return sketch_smem(n, m).total <= 227 * 1024 && (size_t)n * (m + 1) * 4 <= 227 * 1024;
+}
+
+template <class Src, typename Tin, int NMT, int MB>
+static cudaError_t sketch_launch(const Src& src, const TcScratch& sc, int n, int max_items, cudaStream_t st) {
+    const size_t sm = sketch_smem(n, sc.m).total;
+    ZS_TRY(set_smem(k_sketch<Src, Tin, NMT, MB>, sm));
+    k_sketch<Src, Tin, NMT, MB><<<max_items * kSketchCL, 256, sm, st>>>(src, sc, n);
+    return cudaGetLastError();
+}
+
+template <class Src, typename Tin>
+static cudaError_t sketch_dispatch(const Src& src, const TcScratch& sc, int n, int max_items, cudaStream_t st) {
+    if (n <= 128) return sc.m <= 32 ? sketch_launch<Src, Tin, 1, 32>(src, sc, n, max_items, st)
+                                    : sketch_launch<Src, Tin, 1, 64>(src, sc, n, max_items, st);
+    if (n <= 256) return sc.m <= 32 ? sketch_launch<Src, Tin, 2, 32>(src, sc, n, max_items, st)
+                                    : sketch_launch<Src, Tin, 2, 64>(src, sc, n, max_items, st);
+    return sketch_launch<Src, Tin, 4, 32>(src, sc, n, max_items, st);
+}
+
 template <class Src, typename Tin, bool REF, bool QUERY>
 static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
-                           int ews_ctas, int num_sms, int proj_per_sm, cudaStream_t st) {
+                           int ews_ctas, int num_sms, const Tuning& tu, cudaStream_t st) {
     const int ntile = (n + 127) / 128;
     const int npairs = ntile * (ntile + 1) / 2;
     const int gi = std::min(max_items, 65535);
-    {
-        prof::Scope ps(QUERY ? "gram_lo_query" : "gram_lo", st);
-        k_gram_lo<Src, Tin><<<dim3(npairs, gi), 256, 0, st>>>(src, sc, n);
-    }
-    ZS_TRY(cudaGetLastError());
-    {
+    const int proj_per_sm = tu.project_ctas_per_sm;
+    if (tu.fused_sketch && sketch_fits(n, sc.m)) {
+        {
+            prof::Scope ps(QUERY ? "sketch_query" : "sketch", st);
+            ZS_TRY((sketch_dispatch<Src, Tin>(src, sc, n, max_items, st)));
+        }
+        {
+            const size_t sm = (size_t)n * (sc.m + 1) * 4;
+            ZS_TRY(set_smem(k_orth<Src>, sm));
+            prof::Scope ps(QUERY ? "orth_query" : "orth", st);
+            k_orth<Src><<<gi, 256, sm, st>>>(src, sc, n);
+            ZS_TRY(cudaGetLastError());
+        }
+    } else {
+        {
+            prof::Scope ps(QUERY ? "gram_lo_query" : "gram_lo", st);
+            k_gram_lo<Src, Tin><<<dim3(npairs, gi), 256, 0, st>>>(src, sc, n);
+        }
+        ZS_TRY(cudaGetLastError());
         bool yglob;
         const size_t sm = tc_subspace_smem(n, sc.m, yglob);
         const int gs = std::min(gi, yglob ? ews_ctas : 65535);
@@ -75,17 +109,20 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
             ZS_TRY(set_smem(k_subspace<Src, 64>, sm));
             k_subspace<Src, 64><<<gs, 256, sm, st>>>(src, sc, n, yglob ? 1 : 0);
         }
+        ZS_TRY(cudaGetLastError());
     }
-    ZS_TRY(cudaGetLastError());
     {
-        const size_t sm = tc_project_smem(n, sc.m);
+        const size_t sm = project_smem_bytes(sc.m);
         ZS_TRY(set_smem(k_project<Src, Tin>, sm));
         prof::Scope ps(QUERY ? "project_query" : "project", st);
         const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * proj_per_sm);
         k_project<Src, Tin><<<std::max(gp, 1), 256, sm, st>>>(src, sc, n);
     }
     ZS_TRY(cudaGetLastError());
-    {
+    if (!REF && sc.m <= 32) {
+        prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
+        k_rr_core_reg<Src><<<(max_items + 3) / 4, 128, 0, st>>>(src, sc, kw);
+    } else {
         const size_t per = rr_warp_bytes<REF>(sc.m);
         const int wpc = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / per));
         const size_t sm = per * wpc;
@@ -161,7 +198,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         if (tc) {
             TcScratch sc;
             sc.G = (float*)a.G;
-            sc.Qb = (__nv_bfloat16*)a.qb;
+            sc.Qf = (float*)a.qb;
             sc.Y = (float*)a.ys;
             sc.ews = a.ews;
             sc.ews_ctas = std::max(1, a.ews_ctas);
@@ -170,7 +207,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
             SrcQuery src{a};
             ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
-                                                        tu.project_ctas_per_sm, st)));
+                                                        tu, st)));
             {
                 const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
                 ZS_TRY(set_smem(k_bfix, sm));

@@ -82,8 +82,8 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         while (ews_ctas > 1 && zs::eig_ws_bytes((int)n, fp64, ews_ctas) > kNoAllocScratchBytes / 2) ews_ctas /= 2;
         ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
     }
-    // per block: its Gram matrix and, on the tensor path, its bf16 subspace
-    // basis and projection block
+    // per block: its Gram matrix (or subspace sketch) and, on the tensor path,
+    // its tf32 subspace basis and projection block
     const bool tc = zs::use_tc_path(fp64, (int)n, flags);
     const size_t mt = tc ? (size_t)zs::tc_width(k, tune.eig_m_extra) : 0;
     if (tc && ews_bytes == 0) {
@@ -92,7 +92,7 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
     }
     auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t qper = r256(2 * mt * (size_t)n);
+    const size_t qper = r256(4 * mt * (size_t)n);
     const size_t proj = r256(4 * mt * (size_t)b);
     // Rayleigh-Ritz scratch of one block (tile partials, Q~^T Q~, Ritz data) with slack for alignment
     const size_t auxp = tc ? r256(4 * mt * mt * ((b + 127) / 128 + 1) + 4 * mt * k + 4 * k + 1024) : 0;

@@ -2,24 +2,25 @@
 // tensor cores.  Used for the blocks of the storage phase (Section 3.2) and for
 // the stacked Sigma V^T matrix of each query's Stitched-SVD (Algorithm 2).
 //
-// The SVD is computed through a Gram matrix, split so that tensor cores carry
-// the O(rows n^2) work without giving up FP32 accuracy:
-//   1. k_gram_lo    G~ = bf16(X)^T bf16(X), fp32 accumulate (mma.sync bf16).
-//                   Only used to locate the dominant subspace (~1e-3 accurate).
-//   2. k_subspace   m columns Q of G~'s dominant subspace: pivoted columns of G~
-//                   and power steps with Gram-Schmidt (SIMT), stored as bf16 Q~.
-//   3. k_project    Y = X Q~ with X split into three bf16 terms (hi + mid +
-//                   lo, ~24 bits): three bf16 tensor products give X Q~ to FP32
-//                   accuracy (Q~ is exact in bf16, so nothing of Q is lost).
-//   4. k_rr         Rayleigh-Ritz on span(Q~): Y^T Y z = theta (Q~^T Q~) z via a
-//                   Cholesky of Q~^T Q~ and the small Jacobi core; then
-//                   sigma = sqrt(theta), V = Q~ Z, U = Y Z Sigma^{-1}.
-// Accuracy of sigma, U, V is set by step 3-4 (FP32 products of the exact data
+// The SVD is a Rayleigh-Ritz step on a sketched subspace, arranged so that
+// tensor cores carry the O(rows n m) work without giving up FP32 accuracy:
+//   1. k_sketch     S = X^T (X Omega), Omega random signs (bf16 operands, fp32
+//                   accumulate), by a cluster of CTAs per item; only locates
+//                   the dominant subspace.  (k_gram_lo + k_subspace: the same
+//                   from the bf16 Gram, for shapes outside the sketch's limits.)
+//   2. k_orth       Q~ = orthonormal basis of S (two-pass Gram-Schmidt),
+//                   rounded to tf32, and Q~^T Q~.
+//   3. k_project    Y = X Q~ with X split into two tf32 terms: Y to FP32
+//                   accuracy (Q~ is exact in tf32, so nothing of Q is lost).
+//   4. k_rr_core    Rayleigh-Ritz on span(Q~): Y^T Y z = theta (Q~^T Q~) z
+//                   (register core for m <= 32, else the shared-memory core);
+//      k_rr_out     sigma = sqrt(theta), V = Q~ Z, U = Y Z Sigma^{-1}.
+// Accuracy of sigma, U, V is set by steps 3-4 (FP32 products of the exact data
 // against an exact basis); steps 1-2 only decide how good the subspace is,
-// which subspace iteration makes exponentially good in
-// (lambda_{m+1} / lambda_k).
+// which is exponentially good in lambda_{m+1} / lambda_k.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "zs_internal.h"
@@ -102,7 +103,7 @@ struct SrcQuery {
 // Scratch for the tensor path (per launch).
 struct TcScratch {
     float* G;               // items x n x n
-    __nv_bfloat16* Qb;      // items x n x m
+    float* Qf;              // items x n x m: Q~, values exact in tf32
     float* Y;               // (sum of rows) x m, row offsets from Src::ybase
     void* ews;              // per-CTA workspace (subspace Y block), ews_ctas x n x (m+1) floats
     int ews_ctas;
@@ -312,13 +313,13 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
             __syncthreads();
             mgs_orth<float>(Q, ldq, n, m, red, coef);
         }
-        __nv_bfloat16* Qb = sc.Qb + (size_t)item * n * m;
+        float* Qf = sc.Qf + (size_t)item * n * m;
         __syncthreads();
         for (int e = tid; e < n * m; e += nt) {
             const int i = e / m, c = e - (e / m) * m;
-            const __nv_bfloat16 h = __float2bfloat16_rn(Q[i * ldq + c]);
-            Qb[e] = h;
-            Q[i * ldq + c] = __bfloat162float(h);       // Q~ as it will be used
+            const float h = __uint_as_float(to_tf32(Q[i * ldq + c]));
+            Qf[e] = h;
+            Q[i * ldq + c] = h;                         // Q~ as it will be used
         }
         __syncthreads();
         // C = Q~^T Q~ (exact products of bf16 values, fp32 sums)
@@ -335,22 +336,33 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
 }
 
 // ---------------------------------------------------------------------------
-// 3. Y = X Q~ for 128-row tiles: X split into three bf16 terms (three products,
-//    smallest term first).
+// 3. Y = X Q~ for 128-row tiles on tf32 tensor cores: X = X_hi + X_lo with both
+//    terms tf32 (~22 significant bits; bf16 inputs are exact in X_hi alone) and
+//    Q~ exact in tf32, so Y carries FP32 accuracy.  X and Q~ arrive in 32-column
+//    chunks by cp.async into a double buffer; fragments are split in registers.
 // ---------------------------------------------------------------------------
+constexpr int kPjKC = 32;              // columns per chunk
+constexpr int kPjLDX = kPjKC + 4;      // X stage row stride (floats): conflict-free A fragments
+__host__ __device__ __forceinline__ int pj_ldq(int m) { return (m + 31) / 32 * 32 + 8; }   // = 8 mod 32
+__host__ __device__ __forceinline__ size_t pj_stage_floats(int m) {
+    return (size_t)128 * kPjLDX + (size_t)kPjKC * pj_ldq(m);
+}
+__host__ __device__ __forceinline__ size_t project_smem_bytes(int m) {
+    const size_t st = 2 * pj_stage_floats(m) * 4;
+    const size_t ys = (size_t)128 * (m + 1) * 4;          // Y tile for Y^T Y, reuses the stages
+    return st > ys ? st : ys;
+}
+
 template <class Src, typename Tin>
 __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
-    extern __shared__ __align__(16) char dsm[];
-    constexpr int KC = 64, LDX = 72;               // bf16_ld(64)
-    const int m = sc.m, ldqs = bf16_ld(m);
-    __nv_bfloat16* Qs = (__nv_bfloat16*)dsm;                      // n x ldqs
-    __nv_bfloat16* Xh = Qs + (size_t)((n + 15) / 16 * 16) * ldqs;    // 128 x LDX
-    __nv_bfloat16* Xm = Xh + 128 * LDX;
-    __nv_bfloat16* Xl = Xm + 128 * LDX;
+    extern __shared__ __align__(16) float fsm[];
+    const int m = sc.m, ldq = pj_ldq(m), ntn = m / 8;
+    const size_t sf = pj_stage_floats(m);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
     const int64_t ld = src.ld();
-    const int ntn = m / 8;
-    int loaded = -1;
+    const int nch = (n + kPjKC - 1) / kPjKC;
+    constexpr bool kF32 = std::is_same<Tin, float>::value;
     const int64_t ntiles = src.ntiles();
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int item, rt;
@@ -358,122 +370,103 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
         const int rows = src.rows(item);
         const int r0 = rt * 128;
         if (r0 >= rows) continue;
-        const Tin* X = (const Tin*)src.X(item, sizeof(Tin));
-        __syncthreads();
-        if (loaded != item) {
-            const __nv_bfloat16* Qg = sc.Qb + (size_t)item * n * m;
-            const int npad = (n + 15) / 16 * 16;
-            for (int e = tid; e < npad * m; e += 256) {
-                const int l = e / m, c = e - (e / m) * m;
-                Qs[l * ldqs + c] = (l < n) ? Qg[(size_t)l * m + c] : __float2bfloat16_rn(0.f);
+        const char* X = (const char*)src.X(item, sizeof(Tin));
+        const float* Qg = sc.Qf + (size_t)item * n * m;
+        const bool async_x = kF32 && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        const bool async_q = (m % 4 == 0) && ((reinterpret_cast<uintptr_t>(Qg) & 15) == 0);
+        // stage chunk c into buffer b: X rows r0.., columns 32c..; Q~ rows 32c..
+        auto issue = [&](int c, int b) {
+            float* Xs = fsm + (size_t)b * sf;
+            float* Qs = Xs + 128 * kPjLDX;
+            const int k0 = c * kPjKC;
+            for (int f = tid; f < 128 * (kPjKC / 4); f += 256) {
+                const int r = f / (kPjKC / 4), c4 = (f - r * (kPjKC / 4)) * 4;
+                const int gr = r0 + r, gc = k0 + c4;
+                float* dst = Xs + r * kPjLDX + c4;
+                if (async_x) {
+                    const int nb = (gr < rows && gc < n) ? 4 * min(4, n - gc) : 0;
+                    const float* sp = nb ? (const float*)X + (size_t)gr * ld + gc : (const float*)X;
+                    cp_async16(dst, sp, nb);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        float v = 0.f;
+                        if (gr < rows && gc + e < n) {
+                            const Tin* p = (const Tin*)X + (size_t)gr * ld + gc + e;
+                            if constexpr (kF32) v = __ldg(p);
+                            else v = __bfloat162float(*p);
+                        }
+                        dst[e] = v;
+                    }
+                }
             }
-            loaded = item;
-        }
+            for (int f = tid; f < kPjKC * (ldq / 4); f += 256) {
+                const int r = f / (ldq / 4), c4 = (f - r * (ldq / 4)) * 4;
+                const int gr = k0 + r;
+                float* dst = Qs + r * ldq + c4;
+                if (async_q) {
+                    const int nb = (gr < n && c4 < m) ? 16 : 0;
+                    cp_async16(dst, nb ? Qg + (size_t)gr * m + c4 : Qg, nb);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) dst[e] = (gr < n && c4 + e < m) ? Qg[(size_t)gr * m + c4 + e] : 0.f;
+                }
+            }
+            cp_async_commit();
+        };
         float acc[8][4];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-        // each thread stages 8 groups of 4 consecutive values per 128 x 64 chunk;
-        // the next chunk's loads are issued before the current chunk's MMAs
-        const bool xal = std::is_same<Tin, float>::value && (ld % 4 == 0) && (n % 4 == 0) &&
-                         ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-        const auto cx = src.ctx(item, sizeof(Tin));
-        float pre[8][4];
-        auto fetch = [&](int k0) {
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const int f = tid + g * 256;
-                const int r = f >> 4, c = (f & 15) * 4;
-                float* v = pre[g];
-                v[0] = v[1] = v[2] = v[3] = 0.f;
-                if (r0 + r < rows) {
-                    float sc = 1.f;
-                    const Tin* p = src.template row<Tin>(cx, r0 + r, sc) + k0 + c;
-                    if constexpr (std::is_same<Tin, float>::value) {
-                        if (xal && k0 + c + 3 < n) {
-                            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-                            v[0] = q.x * sc; v[1] = q.y * sc; v[2] = q.z * sc; v[3] = q.w * sc;
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (k0 + c + e < n) v[e] = __ldg(p + e) * sc;
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (k0 + c + e < n) v[e] = __bfloat162float(p[e]) * sc;
-                    }
-                }
-            }
-        };
-        fetch(0);
-        for (int k0 = 0; k0 < n; k0 += KC) {
-            __syncthreads();
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const int f = tid + g * 256;
-                const int r = f >> 4, c = (f & 15) * 4;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    // three bf16 terms carry ~24 significant bits of the fp32 value
-                    const float v = pre[g][e];
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                    const float r1 = v - __bfloat162float(hi);
-                    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-                    Xh[r * LDX + c + e] = hi;
-                    Xm[r * LDX + c + e] = mid;
-                    Xl[r * LDX + c + e] = lo;
-                }
+        __syncthreads();                    // previous tile's readers are done with the stages
+        issue(0, 0);
+        for (int c = 0; c < nch; ++c) {
+            if (c + 1 < nch) {
+                issue(c + 1, (c + 1) & 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
-            if (k0 + KC < n) fetch(k0 + KC);
-            const int kmax = min(KC, ((n - k0) + 15) / 16 * 16);
-            for (int kk = 0; kk < kmax; kk += 16) {
-                const int mat = lane >> 3, rr = lane & 7;
-                const int arow = warp * 16 + ((mat & 1) ? 8 : 0) + rr, acol = kk + ((mat >> 1) ? 8 : 0);
-                uint32_t ah[4], am[4], al[4];
-                ldsm_x4(smem_u32(Xh + arow * LDX + acol), ah[0], ah[1], ah[2], ah[3]);
-                ldsm_x4(smem_u32(Xm + arow * LDX + acol), am[0], am[1], am[2], am[3]);
-                ldsm_x4(smem_u32(Xl + arow * LDX + acol), al[0], al[1], al[2], al[3]);
+            const float* Xs = fsm + (size_t)(c & 1) * sf;
+            const float* Qs = Xs + 128 * kPjLDX;
+            const int kk_max = min(kPjKC, n - c * kPjKC);
+            for (int kk = 0; kk < kk_max; kk += 8) {
+                const float* xa = Xs + (warp * 16 + g) * kPjLDX + kk + t4;
+                const float x0 = xa[0], x1 = xa[8 * kPjLDX], x2 = xa[4], x3 = xa[8 * kPjLDX + 4];
+                const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1), h2 = to_tf32(x2), h3 = to_tf32(x3);
+                uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+                if constexpr (kF32) {
+                    l0 = to_tf32(x0 - __uint_as_float(h0));
+                    l1 = to_tf32(x1 - __uint_as_float(h1));
+                    l2 = to_tf32(x2 - __uint_as_float(h2));
+                    l3 = to_tf32(x3 - __uint_as_float(h3));
+                }
+                const float* qb = Qs + (kk + t4) * ldq + g;
 #pragma unroll
-                for (int np = 0; np < 4; ++np) {
-                    if (2 * np >= ntn) break;
-                    const int t = k0 + kk + rr + ((mat & 1) ? 8 : 0);
-                    const int c = np * 16 + ((mat >> 1) ? 8 : 0);
-                    uint32_t b0, b1, b2, b3;
-                    if (2 * np + 1 < ntn) {
-                        ldsm_x4_t(smem_u32(Qs + t * ldqs + c), b0, b1, b2, b3);
-                    } else {
-                        ldsm_x2_t(smem_u32(Qs + t * ldqs + np * 16), b0, b1);
-                        b2 = b3 = 0;
-                    }
-                    mma_bf16(acc[2 * np], al[0], al[1], al[2], al[3], b0, b1);
-                    mma_bf16(acc[2 * np], am[0], am[1], am[2], am[3], b0, b1);
-                    mma_bf16(acc[2 * np], ah[0], ah[1], ah[2], ah[3], b0, b1);
-                    if (2 * np + 1 < ntn) {
-                        mma_bf16(acc[2 * np + 1], al[0], al[1], al[2], al[3], b2, b3);
-                        mma_bf16(acc[2 * np + 1], am[0], am[1], am[2], am[3], b2, b3);
-                        mma_bf16(acc[2 * np + 1], ah[0], ah[1], ah[2], ah[3], b2, b3);
-                    }
+                for (int nt = 0; nt < 8; ++nt) {
+                    if (nt >= ntn) break;
+                    const uint32_t b0 = __float_as_uint(qb[nt * 8]), b1 = __float_as_uint(qb[4 * ldq + nt * 8]);
+                    if constexpr (kF32) mma_tf32(acc[nt], l0, l1, l2, l3, b0, b1);
+                    mma_tf32(acc[nt], h0, h1, h2, h3, b0, b1);
                 }
             }
+            __syncthreads();                // buffer (c & 1) is refilled by the next issue
         }
         float* Y = sc.Y + (size_t)src.ybase(item) * m;
-        __syncthreads();
-        float* Ys = reinterpret_cast<float*>(Xh);      // 128 x (m+1), reuses the X staging
+        float* Ys = fsm;                    // 128 x (m+1)
         const int ldy = m + 1;
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             if (nt >= ntn) break;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int rl = warp * 16 + (lane >> 2) + ((e >> 1) ? 8 : 0);
-                const int c = nt * 8 + 2 * (lane & 3) + (e & 1);
+                const int rl = warp * 16 + g + ((e >> 1) ? 8 : 0);
+                const int cc = nt * 8 + 2 * t4 + (e & 1);
                 const int r = r0 + rl;
-                if (r < rows) Y[(size_t)r * m + c] = acc[nt][e];
-                Ys[rl * ldy + c] = (r < rows) ? acc[nt][e] : 0.f;
+                if (r < rows) Y[(size_t)r * m + cc] = acc[nt][e];
+                Ys[rl * ldy + cc] = (r < rows) ? acc[nt][e] : 0.f;
             }
         }
         __syncthreads();
@@ -481,12 +474,301 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
         float* Hp = sc.Hp + (size_t)tile * m * m;
         const int nr = min(128, rows - r0);
         for (int e = tid; e < m * m; e += 256) {
+            const int a = e / m, cc = e - (e / m) * m;
+            if (cc < a) continue;
+            float h0 = 0.f, h1 = 0.f;
+            int r = 0;
+            for (; r + 1 < nr; r += 2) {
+                h0 = fmaf(Ys[r * ldy + a], Ys[r * ldy + cc], h0);
+                h1 = fmaf(Ys[(r + 1) * ldy + a], Ys[(r + 1) * ldy + cc], h1);
+            }
+            if (r < nr) h0 = fmaf(Ys[r * ldy + a], Ys[r * ldy + cc], h0);
+            const float h = h0 + h1;
+            Hp[a * m + cc] = h;
+            Hp[cc * m + a] = h;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2'. Subspace sketch of one item by a cluster of kSketchCL CTAs that split the
+//     item's 128-row tiles round-robin: S = X^T (X Omega), Omega an n x m
+//     matrix of random signs (bf16 operands, fp32 accumulation) - one step of
+//     the randomized range finder of Halko, Martinsson & Tropp (SIAM Review 53,
+//     2011) applied to the rows' Gram matrix without forming it.  The CTAs'
+//     partial S are summed through distributed shared memory in a fixed order
+//     (each CTA reduces a slice of rows and stores it): S to sc.G as n x m.
+//     Costs O(rows n m) tensor work and one read of X.
+// ---------------------------------------------------------------------------
+constexpr int kSketchCL = 4;
+
+// Random sign of Omega(i, c): the SplitMix64 output function (Steele, Lea &
+// Flood, OOPSLA 2014) of the counter (i, c).
+__device__ __forceinline__ float omega_sign(uint32_t i, uint32_t c) {
+    uint64_t z = (((uint64_t)i << 32) | c) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (z & 1) ? 1.f : -1.f;
+}
+
+// Shared-memory plan of k_sketch (bytes from the dynamic base):
+// [Rx: the bf16 X tile, later the fp32 partial S and the reduced slice |
+//  Bs: bf16 Omega, npad x bf16_ld(m) | Ws: bf16 W, 128 x bf16_ld(m)]
+struct SketchSmem {
+    size_t rx, bs, ws, total;
+};
+__host__ __device__ __forceinline__ SketchSmem sketch_smem(int n, int m) {
+    auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+    const size_t npad = (size_t)(n + 15) / 16 * 16;
+    const size_t chunk = (npad + kSketchCL - 1) / kSketchCL;
+    size_t rx = r16((size_t)128 * bf16_ld((int)npad) * 2);
+    const size_t sred = r16((npad + chunk) * (m + 1) * 4);
+    rx = rx > sred ? rx : sred;
+    SketchSmem s;
+    s.rx = rx;
+    s.bs = r16(npad * bf16_ld(m) * 2);
+    s.ws = r16((size_t)128 * bf16_ld(m) * 2);
+    s.total = s.rx + s.bs + s.ws;
+    return s;
+}
+
+// NMT: 16-row tiles of S per warp (n <= 128 NMT); MB: bound on m.
+template <class Src, typename Tin, int NMT, int MB>
+__global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * MB <= 64) ? 2 : 1)
+    k_sketch(Src src, TcScratch sc, int n) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) char dsm[];
+    const int item = blockIdx.x / kSketchCL;
+    const int cr = (int)cl.block_rank();
+    if (item >= src.count()) return;                 // the whole cluster leaves together
+    const int m = sc.m, rows = src.rows(item);
+    const int ntl = (rows + 127) / 128;
+    const int npad = (n + 15) / 16 * 16;
+    const int ldx = bf16_ld(npad), ldb = bf16_ld(m), lds = m + 1;
+    const SketchSmem L = sketch_smem(n, m);
+    __nv_bfloat16* Xs = (__nv_bfloat16*)dsm;
+    float* Sp = (float*)dsm;                          // npad x lds (after the tiles)
+    const int chunk = (npad + kSketchCL - 1) / kSketchCL;
+    float* Ssl = Sp + (size_t)npad * lds;              // chunk x lds
+    __nv_bfloat16* Bs = (__nv_bfloat16*)(dsm + L.rx);
+    __nv_bfloat16* Ws = (__nv_bfloat16*)(dsm + L.rx + L.bs);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mat = lane >> 3, rr = lane & 7;
+    const int ntn = m / 8;
+    const int64_t ld = src.ld();
+    const Tin* X = (const Tin*)src.X(item, sizeof(Tin));
+    const bool xal = std::is_same<Tin, float>::value && (ld % 4 == 0) && (n % 4 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const auto cx = src.ctx(item, sizeof(Tin));
+
+    for (int e = tid; e < npad * m; e += 256) {
+        const int l = e / m, c = e - (e / m) * m;
+        Bs[l * ldb + c] = __float2bfloat16_rn(l < n ? omega_sign((uint32_t)l, (uint32_t)c) : 0.f);
+    }
+    float sacc[NMT][MB / 8][4];
+#pragma unroll
+    for (int a = 0; a < NMT; ++a)
+#pragma unroll
+        for (int b = 0; b < MB / 8; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sacc[a][b][c] = 0.f;
+    for (int t = cr; t < ntl; t += kSketchCL) {
+        const int r0 = t * 128;
+        __syncthreads();
+        // X tile -> bf16 Xs (zero rows past `rows`, columns past n)
+        const int q4 = npad / 4;
+        for (int f0 = 0; f0 < 128 * q4; f0 += 256 * 8) {
+            float v[8][4];
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) {
+                const int f = f0 + tid + gg * 256;
+                const int r = f / q4, c = (f - r * q4) * 4;
+                v[gg][0] = v[gg][1] = v[gg][2] = v[gg][3] = 0.f;
+                if (f < 128 * q4 && r0 + r < rows) {
+                    float s = 1.f;
+                    const Tin* p = src.template row<Tin>(cx, r0 + r, s) + c;
+                    if constexpr (std::is_same<Tin, float>::value) {
+                        if (xal && c + 3 < n) {
+                            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+                            v[gg][0] = q.x * s; v[gg][1] = q.y * s; v[gg][2] = q.z * s; v[gg][3] = q.w * s;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (c + e < n) v[gg][e] = __ldg(p + e) * s;
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (c + e < n) v[gg][e] = __bfloat162float(p[e]) * s;
+                    }
+                }
+            }
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) {
+                const int f = f0 + tid + gg * 256;
+                if (f >= 128 * q4) break;
+                const int r = f / q4, c = (f - r * q4) * 4;
+                uint32_t* dp = reinterpret_cast<uint32_t*>(Xs + r * ldx + c);
+                dp[0] = pack_bf16(__float2bfloat16_rn(v[gg][0]), __float2bfloat16_rn(v[gg][1]));
+                dp[1] = pack_bf16(__float2bfloat16_rn(v[gg][2]), __float2bfloat16_rn(v[gg][3]));
+            }
+        }
+        __syncthreads();
+        // W = Xs Omega (warp: rows 16 warp .. +15, all m columns) -> bf16 Ws
+        {
+            float wacc[MB / 8][4];
+#pragma unroll
+            for (int b = 0; b < MB / 8; ++b)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) wacc[b][c] = 0.f;
+            const int arow = warp * 16 + ((mat & 1) ? 8 : 0) + rr;
+            for (int kk = 0; kk < npad; kk += 16) {
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4(smem_u32(Xs + arow * ldx + kk + ((mat >> 1) ? 8 : 0)), a0, a1, a2, a3);
+#pragma unroll
+                for (int np = 0; np < MB / 16; ++np) {
+                    if (2 * np >= ntn) break;
+                    const int tt = kk + rr + ((mat & 1) ? 8 : 0);
+                    uint32_t b0, b1, b2, b3;
+                    if (2 * np + 1 < ntn) {
+                        ldsm_x4_t(smem_u32(Bs + tt * ldb + np * 16 + ((mat >> 1) ? 8 : 0)), b0, b1, b2, b3);
+                    } else {
+                        ldsm_x2_t(smem_u32(Bs + tt * ldb + np * 16), b0, b1);
+                        b2 = b3 = 0;
+                    }
+                    mma_bf16(wacc[2 * np], a0, a1, a2, a3, b0, b1);
+                    if (2 * np + 1 < ntn) mma_bf16(wacc[2 * np + 1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < MB / 8; ++nt) {
+                if (nt >= ntn) break;
+                const int rl = warp * 16 + (lane >> 2);
+                const int c = nt * 8 + 2 * (lane & 3);
+                *reinterpret_cast<uint32_t*>(Ws + rl * ldb + c) =
+                    pack_bf16(__float2bfloat16_rn(wacc[nt][0]), __float2bfloat16_rn(wacc[nt][1]));
+                *reinterpret_cast<uint32_t*>(Ws + (rl + 8) * ldb + c) =
+                    pack_bf16(__float2bfloat16_rn(wacc[nt][2]), __float2bfloat16_rn(wacc[nt][3]));
+            }
+        }
+        __syncthreads();
+        // S += Xs^T Ws (warp: S rows 16 NMT warp .. , K = the tile's 128 rows)
+        {
+            const int i0 = warp * 16 * NMT;
+            if (i0 < npad) {
+                for (int kk = 0; kk < 128; kk += 16) {
+                    uint32_t bf[MB / 8][2];
+#pragma unroll
+                    for (int np = 0; np < MB / 16; ++np) {
+                        if (2 * np >= ntn) break;
+                        const int tt = kk + rr + ((mat & 1) ? 8 : 0);
+                        if (2 * np + 1 < ntn) {
+                            ldsm_x4_t(smem_u32(Ws + tt * ldb + np * 16 + ((mat >> 1) ? 8 : 0)), bf[2 * np][0],
+                                      bf[2 * np][1], bf[2 * np + 1][0], bf[2 * np + 1][1]);
+                        } else {
+                            ldsm_x2_t(smem_u32(Ws + tt * ldb + np * 16), bf[2 * np][0], bf[2 * np][1]);
+                        }
+                    }
+#pragma unroll
+                    for (int mt = 0; mt < NMT; ++mt) {
+                        const int ib = i0 + mt * 16;
+                        if (ib >= npad) break;
+                        uint32_t a0, a1, a2, a3;
+                        const int tt = kk + rr + ((mat >> 1) ? 8 : 0);
+                        ldsm_x4_t(smem_u32(Xs + tt * ldx + ib + ((mat & 1) ? 8 : 0)), a0, a1, a2, a3);
+#pragma unroll
+                        for (int nt = 0; nt < MB / 8; ++nt) {
+                            if (nt >= ntn) break;
+                            mma_bf16(sacc[mt][nt], a0, a1, a2, a3, bf[nt][0], bf[nt][1]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // cluster sum of S in a fixed order: CTA cr reduces rows [cr chunk, ..) and stores them
+    __syncthreads();
+    {
+        const int i0 = warp * 16 * NMT;
+#pragma unroll
+        for (int mt = 0; mt < NMT; ++mt) {
+            const int ib = i0 + mt * 16;
+            if (ib >= npad) break;
+#pragma unroll
+            for (int nt = 0; nt < MB / 8; ++nt) {
+                if (nt >= ntn) break;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = ib + (lane >> 2) + ((e >> 1) ? 8 : 0);
+                    const int c = nt * 8 + 2 * (lane & 3) + (e & 1);
+                    Sp[i * lds + c] = sacc[mt][nt][e];
+                }
+            }
+        }
+    }
+    cl.sync();
+    {
+        const int lo = cr * chunk, hi = min(n, lo + chunk);
+        const float* rp[kSketchCL];
+#pragma unroll
+        for (int q = 0; q < kSketchCL; ++q) rp[q] = cl.map_shared_rank(Sp, q);
+        float* Sg = sc.G + (size_t)item * n * m;
+        for (int e = tid; e < (hi - lo) * m; e += 256) {
+            const int i = lo + e / m, c = e - (e / m) * m;
+            float v[kSketchCL];
+#pragma unroll
+            for (int q = 0; q < kSketchCL; ++q) v[q] = rp[q][i * lds + c];
+            float s = 0.f;
+#pragma unroll
+            for (int q = 0; q < kSketchCL; ++q) s += v[q];
+            Sg[(size_t)i * m + c] = s;
+        }
+    }
+    cl.sync();                                     // peers may still read this CTA's partial until here
+}
+
+// ---------------------------------------------------------------------------
+// 2''. Orthonormal basis of the sketch, one CTA per item: S (n x m, sc.G) ->
+//      two-pass Gram-Schmidt with replacement of dependent columns -> Q~
+//      rounded to tf32 (exact operand of the projection) and C = Q~^T Q~.
+// ---------------------------------------------------------------------------
+template <class Src>
+__global__ void __launch_bounds__(256) k_orth(Src src, TcScratch sc, int n) {
+    extern __shared__ __align__(16) float osm[];
+    __shared__ float red[32];
+    __shared__ float coef[ZS_MAXM];
+    const int m = sc.m, lds = m + 1, tid = threadIdx.x;
+    float* Q = osm;                                  // n x lds
+    for (int item = blockIdx.x; item < src.count(); item += gridDim.x) {
+        const float* Sg = sc.G + (size_t)item * n * m;
+        __syncthreads();
+        for (int e = tid; e < n * m; e += 256) Q[(e / m) * lds + (e % m)] = Sg[e];
+        __syncthreads();
+        mgs_orth<float>(Q, lds, n, m, red, coef);
+        float* Qf = sc.Qf + (size_t)item * n * m;
+        for (int e = tid; e < n * m; e += 256) {
+            const int l = e / m, c = e - (e / m) * m;
+            const float h = __uint_as_float(to_tf32(Q[l * lds + c]));
+            Qf[e] = h;
+            Q[l * lds + c] = h;                      // Q~ as it will be used
+        }
+        __syncthreads();
+        // C = Q~^T Q~ (exact products of tf32 values, fp32 sums)
+        float* Cq = sc.Cq + (size_t)item * m * m;
+        for (int e = tid; e < m * m; e += 256) {
             const int a = e / m, c = e - (e / m) * m;
             if (c < a) continue;
-            float h = 0.f;
-            for (int r = 0; r < nr; ++r) h += Ys[r * ldy + a] * Ys[r * ldy + c];
-            Hp[a * m + c] = h;
-            Hp[c * m + a] = h;
+            float h0 = 0.f, h1 = 0.f;
+            int i = 0;
+            for (; i + 1 < n; i += 2) {
+                h0 = fmaf(Q[i * lds + a], Q[i * lds + c], h0);
+                h1 = fmaf(Q[(i + 1) * lds + a], Q[(i + 1) * lds + c], h1);
+            }
+            if (i < n) h0 = fmaf(Q[i * lds + a], Q[i * lds + c], h0);
+            Cq[a * m + c] = h0 + h1;
+            Cq[c * m + a] = h0 + h1;
         }
     }
 }
@@ -635,6 +917,176 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
 }
 
 // ---------------------------------------------------------------------------
+// 4a'. Rayleigh-Ritz core in registers (m <= 32, FP32 cores): one warp per
+//      item, lane l owning column l of each m x m matrix (padded to 32):
+//        C = Q~^T Q~ = L L^T          Cholesky, pivots broadcast by shuffle
+//        H' = L^-1 H L^-T             two forward substitutions (H symmetric)
+//        H' = G G^T                   Cholesky
+//        G J = W Theta^(1/2)          one-sided (Hestenes) Jacobi on G's columns
+//      G is R^T for R^T R = H', so the orthogonalised columns of G are the
+//      eigenvectors of H' scaled by sqrt(theta): no rotation accumulator.
+//      Then Z = L^-T W for the kw largest theta.  Pairing is the round-robin
+//      schedule of zs_linalg.cuh (index 0 fixed, 1..31 rotating), in closed
+//      form so that each lane finds its partner without a table.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int rr_partner32(int x, int r) {
+    if (x == 0) return (r + 30) % 31 + 1;
+    int v = (2 * r - 2 - (x - 1)) % 31;
+    if (v < 0) v += 31;
+    const int y = v + 1;
+    return y == x ? 0 : y;
+}
+
+// In-register Cholesky of the warp's symmetric 32 x 32 matrix (lane l holds
+// column l).  On return lane l holds column l of L (zeros above the
+// diagonal); a pivot <= 0 gives a zero column.
+__device__ __forceinline__ void warp_chol32(float (&a)[32], int lane) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const float piv = __shfl_sync(0xffffffffu, a[j], j);
+        const float d = piv > 0.f ? sqrtf(piv) : 0.f;
+        const float inv = d > 0.f ? 1.f / d : 0.f;
+        const float slj = a[j] * inv;                       // L[lane][j] for lane > j
+#pragma unroll
+        for (int i = j + 1; i < 32; ++i) {
+            const float lij = __shfl_sync(0xffffffffu, a[i], j) * inv;
+            if (lane > j) a[i] = fmaf(-lij, slj, a[i]);
+        }
+        if (lane == j) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) a[i] = i < j ? 0.f : (i == j ? d : a[i] * inv);
+        }
+    }
+}
+
+// x = L^-1 h for every lane's own vector h (L: lane p holds column p).
+__device__ __forceinline__ void warp_fsub32(const float (&L)[32], const float (&h)[32], float (&x)[32]) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        float acc = h[i];
+#pragma unroll
+        for (int p = 0; p < i; ++p) acc = fmaf(-__shfl_sync(0xffffffffu, L[i], p), x[p], acc);
+        const float dii = __shfl_sync(0xffffffffu, L[i], i);
+        x[i] = dii > 0.f ? acc / dii : 0.f;
+    }
+}
+
+// z = L^-T w for every lane's own vector w.
+__device__ __forceinline__ void warp_bsub32(const float (&L)[32], const float (&w)[32], float (&z)[32]) {
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        float acc = w[i];
+#pragma unroll
+        for (int p = i + 1; p < 32; ++p) acc = fmaf(-__shfl_sync(0xffffffffu, L[p], i), z[p], acc);
+        const float dii = __shfl_sync(0xffffffffu, L[i], i);
+        z[i] = dii > 0.f ? acc / dii : 0.f;
+    }
+}
+
+template <class Src>
+__global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int kw) {
+    __shared__ float tr[4][32 * 33];                  // per-warp transpose buffer
+    const int m = sc.m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    float* T = tr[warp];
+    // one item per warp (the launch covers every item): the register arrays
+    // below stay in registers only while no loop encloses the unrolled code
+    const int item = blockIdx.x * wpc + warp;
+    if (item >= src.count()) return;
+    {
+        const int rows = src.rows(item);
+        const int ntiles = (rows + 127) / 128;
+        const float* Hp = sc.Hp + (size_t)src.tile0(item) * m * m;
+        const float* Cq = sc.Cq + (size_t)item * m * m;
+        float lc[32], v[32], x[32];
+        // columns of H (sum of the tiles, fixed order) and of C, identity-padded
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            v[i] = 0.f;
+            lc[i] = (i < m && lane < m) ? Cq[i * m + lane] : (i == lane ? 1.f : 0.f);
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            const float* hp = Hp + (size_t)t * m * m;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i < m && lane < m) v[i] += hp[i * m + lane];
+        }
+        warp_chol32(lc, lane);
+        warp_fsub32(lc, v, x);                         // X = L^-1 H, column `lane`
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) T[i * 33 + lane] = x[i];
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = T[lane * 33 + i];   // row `lane` of X
+        warp_fsub32(lc, v, x);                         // H' = L^-1 X^T, column `lane`
+        warp_chol32(x, lane);                          // H' = G G^T, column `lane` of G
+        // one-sided Jacobi on the columns of G
+        float al = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+        const float tol = 4.f * 1.1920929e-7f;
+        for (int sweep = 0; sweep < 30; ++sweep) {
+            int rotated = 0;
+            for (int r = 0; r < 31; ++r) {
+                const int pr = rr_partner32(lane, r);
+                const bool isp = lane < pr;
+                float g = 0.f;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    v[i] = __shfl_sync(0xffffffffu, x[i], pr);
+                    g = fmaf(x[i], v[i], g);
+                }
+                const float ao = __shfl_sync(0xffffffffu, al, pr);
+                const float app = isp ? al : ao, aqq = isp ? ao : al;
+                float c = 1.f, s = 0.f;
+                if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
+                    const float zeta = (aqq - app) / (2.f * g);
+                    const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    c = 1.f / sqrtf(1.f + t * t);
+                    s = c * t;
+                    al = isp ? app - t * g : aqq + t * g;
+                    rotated = 1;
+                }
+                if (isp) {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) x[i] = c * x[i] - s * v[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) x[i] = s * v[i] + c * x[i];
+                }
+            }
+            if (!__any_sync(0xffffffffu, rotated)) break;
+            al = 0.f;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+        }
+        al = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+        const float sg = sqrtf(al);
+        const float inv = sg > 0.f ? 1.f / sg : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] *= inv;      // w = unit eigenvector of H'
+        // rank of this lane's theta (descending, lower lane first on ties)
+        int rk = 0;
+#pragma unroll
+        for (int o = 0; o < 32; ++o) {
+            const float ot = __shfl_sync(0xffffffffu, al, o);
+            rk += (ot > al) || (ot == al && o < lane);
+        }
+        warp_bsub32(lc, x, v);                         // z = L^-T w
+        if (rk < kw) {
+            float* Zg = sc.Zs + (size_t)item * m * kw;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                if (i < m) Zg[i * kw + rk] = v[i];
+            sc.th[(size_t)item * kw + rk] = al;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 4b. Outputs per item: sigma = sqrt(theta), V = Q~ Z (signed), U = Y Z Sigma^-1.
 // ---------------------------------------------------------------------------
 template <class Src, bool QUERY>
@@ -650,7 +1102,7 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
     for (int item = blockIdx.x; item < src.count(); item += gridDim.x) {
         const int rows = src.rows(item);
         const float* Y = sc.Y + (size_t)src.ybase(item) * m;
-        const __nv_bfloat16* Qb = sc.Qb + (size_t)item * n * m;
+        const float* Qf = sc.Qf + (size_t)item * n * m;
         __syncthreads();
         for (int e = tid; e < m * kw; e += nt) Zsm[e] = sc.Zs[(size_t)item * m * kw + e];
         int kcap;
@@ -669,8 +1121,8 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
         for (int e = tid; e < n * kw; e += nt) {
             const int l = e / kw, c = e - (e / kw) * kw;
             float v = 0.f;
-            const __nv_bfloat16* qr = Qb + (size_t)l * m;
-            for (int a = 0; a < m; ++a) v += __bfloat162float(qr[a]) * Zsm[a * kw + c];
+            const float* qr = Qf + (size_t)l * m;
+            for (int a = 0; a < m; ++a) v += qr[a] * Zsm[a * kw + c];
             Vs[e] = v;
         }
         __syncthreads();
