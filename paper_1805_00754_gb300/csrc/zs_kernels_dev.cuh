@@ -662,6 +662,22 @@ __global__ void __launch_bounds__(256) k_stack(QueryArgs a) {
         const T* sg = (const T*)a.sig + (int64_t)blk * k;
         const T* vt = (const T*)a.vt + (int64_t)blk * k * n;
         T* Ms = (T*)a.M + s * k * n;
+        if constexpr (std::is_same<T, float>::value) {
+            if ((n & 3) == 0) {
+                // rows of n/4 float4 groups: row j scaled by sigma_j
+                const int n4 = n >> 2;
+                const float4* v4 = reinterpret_cast<const float4*>(vt);
+                float4* m4 = reinterpret_cast<float4*>(Ms);
+                for (int e = threadIdx.x; e < k * n4; e += blockDim.x) {
+                    const int j = e / n4;
+                    const float sj = __ldg(sg + j);
+                    float4 v = __ldg(v4 + e);
+                    v.x *= sj; v.y *= sj; v.z *= sj; v.w *= sj;
+                    m4[e] = v;
+                }
+                continue;
+            }
+        }
         for (int e = threadIdx.x; e < k * n; e += blockDim.x) Ms[e] = sg[e / n] * vt[e];
     }
 }

@@ -73,6 +73,23 @@ static cudaError_t sketch_dispatch(const Src& src, const TcScratch& sc, int n, i
     return sketch_launch<Src, Tin, 4, 32>(src, sc, n, max_items, st);
 }
 
+template <class Src, int RPL, int CPW>
+static cudaError_t orth_launch(const Src& src, const TcScratch& sc, int n, int max_items, cudaStream_t st) {
+    const size_t sm = (size_t)n * (sc.m + 1) * 4;
+    ZS_TRY(set_smem(k_orth<Src, RPL, CPW>, sm));
+    k_orth<Src, RPL, CPW><<<max_items, 32 * kOrthWarps, sm, st>>>(src, sc, n);
+    return cudaGetLastError();
+}
+
+// rows per lane RPL = n / 32 (n <= 512), columns per warp CPW = m / 16
+template <class Src>
+static cudaError_t orth_dispatch(const Src& src, const TcScratch& sc, int n, int max_items, cudaStream_t st) {
+    if (n <= 256) return sc.m <= 32 ? orth_launch<Src, 8, 2>(src, sc, n, max_items, st)
+                                    : orth_launch<Src, 8, 4>(src, sc, n, max_items, st);
+    return sc.m <= 32 ? orth_launch<Src, 16, 2>(src, sc, n, max_items, st)
+                      : orth_launch<Src, 16, 4>(src, sc, n, max_items, st);
+}
+
 template <class Src, typename Tin, bool REF, bool QUERY>
 static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
                            int ews_ctas, int num_sms, const Tuning& tu, cudaStream_t st) {
@@ -86,11 +103,8 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
             ZS_TRY((sketch_dispatch<Src, Tin>(src, sc, n, max_items, st)));
         }
         {
-            const size_t sm = (size_t)n * (sc.m + 1) * 4;
-            ZS_TRY(set_smem(k_orth<Src>, sm));
             prof::Scope ps(QUERY ? "orth_query" : "orth", st);
-            k_orth<Src><<<gi, 256, sm, st>>>(src, sc, n);
-            ZS_TRY(cudaGetLastError());
+            ZS_TRY((orth_dispatch<Src>(src, sc, n, max_items, st)));
         }
     } else {
         {
@@ -132,7 +146,7 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
     }
     ZS_TRY(cudaGetLastError());
     {
-        const size_t sm = sizeof(float) * ((size_t)sc.m * kw + (size_t)n * kw);
+        const size_t sm = rr_out_smem_bytes(n, sc.m, kw);
         ZS_TRY(set_smem(k_rr_out<Src, QUERY>, sm));
         prof::Scope ps(QUERY ? "rr_out_query" : "rr_out", st);
         k_rr_out<Src, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);

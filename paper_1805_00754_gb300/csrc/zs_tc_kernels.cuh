@@ -337,24 +337,39 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
 
 // ---------------------------------------------------------------------------
 // 3. Y = X Q~ for 128-row tiles on tf32 tensor cores: X = X_hi + X_lo with both
-//    terms tf32 (~22 significant bits; bf16 inputs are exact in X_hi alone) and
+//    terms tf32 (~21 significant bits; bf16 inputs are exact in X_hi alone) and
 //    Q~ exact in tf32, so Y carries FP32 accuracy.  X and Q~ arrive in 32-column
 //    chunks by cp.async into a double buffer; fragments are split in registers.
 // ---------------------------------------------------------------------------
 constexpr int kPjKC = 32;              // columns per chunk
 constexpr int kPjLDX = kPjKC + 4;      // X stage row stride (floats): conflict-free A fragments
+constexpr int kPjStages = 3;
 __host__ __device__ __forceinline__ int pj_ldq(int m) { return (m + 31) / 32 * 32 + 8; }   // = 8 mod 32
 __host__ __device__ __forceinline__ size_t pj_stage_floats(int m) {
     return (size_t)128 * kPjLDX + (size_t)kPjKC * pj_ldq(m);
 }
 __host__ __device__ __forceinline__ size_t project_smem_bytes(int m) {
-    const size_t st = 2 * pj_stage_floats(m) * 4;
-    const size_t ys = (size_t)128 * (m + 1) * 4;          // Y tile for Y^T Y, reuses the stages
+    const size_t st = kPjStages * pj_stage_floats(m) * 4;
+    const size_t ys = (size_t)128 * pj_ldq(m) * 4;          // Y tile for Y^T Y, reuses the stages
     return st > ys ? st : ys;
 }
 
+// tf32 split of one fragment value: x = hi + lo with both terms tf32
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+// Cheaper split for streamed data: hi = x with the 13 low mantissa bits
+// cleared, lo = x - hi (exact in fp32) likewise truncated; x - (hi + lo) is
+// below 2^-20 |x|.  Plain bit operations, no conversion instructions.
+__device__ __forceinline__ void tf32_split_trunc(float x, uint32_t& hi, uint32_t& lo) {
+    hi = __float_as_uint(x) & 0xffffe000u;
+    lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
+}
+
 template <class Src, typename Tin>
-__global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
+__global__ void __launch_bounds__(256, 3) k_project(Src src, TcScratch sc, int n) {
     extern __shared__ __align__(16) float fsm[];
     const int m = sc.m, ldq = pj_ldq(m), ntn = m / 8;
     const size_t sf = pj_stage_floats(m);
@@ -421,27 +436,33 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
             for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
         __syncthreads();                    // previous tile's readers are done with the stages
         issue(0, 0);
+        if (nch > 1) issue(1, 1);
         for (int c = 0; c < nch; ++c) {
-            if (c + 1 < nch) {
-                issue(c + 1, (c + 1) & 1);
+            if (c + 2 < nch) {
+                issue(c + 2, (c + 2) % kPjStages);
+                cp_async_wait<2>();
+            } else if (c + 1 < nch) {
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncthreads();
-            const float* Xs = fsm + (size_t)(c & 1) * sf;
+            const float* Xs = fsm + (size_t)(c % kPjStages) * sf;
             const float* Qs = Xs + 128 * kPjLDX;
             const int kk_max = min(kPjKC, n - c * kPjKC);
             for (int kk = 0; kk < kk_max; kk += 8) {
                 const float* xa = Xs + (warp * 16 + g) * kPjLDX + kk + t4;
-                const float x0 = xa[0], x1 = xa[8 * kPjLDX], x2 = xa[4], x3 = xa[8 * kPjLDX + 4];
-                const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1), h2 = to_tf32(x2), h3 = to_tf32(x3);
-                uint32_t l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+                uint32_t h0, h1, h2, h3, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
                 if constexpr (kF32) {
-                    l0 = to_tf32(x0 - __uint_as_float(h0));
-                    l1 = to_tf32(x1 - __uint_as_float(h1));
-                    l2 = to_tf32(x2 - __uint_as_float(h2));
-                    l3 = to_tf32(x3 - __uint_as_float(h3));
+                    tf32_split_trunc(xa[0], h0, l0);
+                    tf32_split_trunc(xa[8 * kPjLDX], h1, l1);
+                    tf32_split_trunc(xa[4], h2, l2);
+                    tf32_split_trunc(xa[8 * kPjLDX + 4], h3, l3);
+                } else {                    // bf16 values are exact in tf32
+                    h0 = __float_as_uint(xa[0]);
+                    h1 = __float_as_uint(xa[8 * kPjLDX]);
+                    h2 = __float_as_uint(xa[4]);
+                    h3 = __float_as_uint(xa[8 * kPjLDX + 4]);
                 }
                 const float* qb = Qs + (kk + t4) * ldq + g;
 #pragma unroll
@@ -452,40 +473,55 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
                     mma_tf32(acc[nt], h0, h1, h2, h3, b0, b1);
                 }
             }
-            __syncthreads();                // buffer (c & 1) is refilled by the next issue
+            __syncthreads();                // buffer (c % kPjStages) is refilled two chunks later
         }
         float* Y = sc.Y + (size_t)src.ybase(item) * m;
-        float* Ys = fsm;                    // 128 x (m+1)
-        const int ldy = m + 1;
+        float* Ys = fsm;                    // 128 x ldq, zero past row `rows` and column m
+        const int mp = (m + 15) / 16 * 16;
 #pragma unroll
         for (int nt = 0; nt < 8; ++nt) {
             if (nt >= ntn) break;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int rl = warp * 16 + g + ((e >> 1) ? 8 : 0);
-                const int cc = nt * 8 + 2 * t4 + (e & 1);
+            for (int h = 0; h < 2; ++h) {
+                const int rl = warp * 16 + g + 8 * h;
+                const int cc = nt * 8 + 2 * t4;
                 const int r = r0 + rl;
-                if (r < rows) Y[(size_t)r * m + cc] = acc[nt][e];
-                Ys[rl * ldy + cc] = (r < rows) ? acc[nt][e] : 0.f;
+                const float v0 = r < rows ? acc[nt][2 * h] : 0.f, v1 = r < rows ? acc[nt][2 * h + 1] : 0.f;
+                if (r < rows) *reinterpret_cast<float2*>(Y + (size_t)r * m + cc) = make_float2(v0, v1);
+                Ys[rl * ldq + cc] = v0;
+                Ys[rl * ldq + cc + 1] = v1;
             }
         }
+        if (mp > m)
+            for (int e = tid; e < 128 * (mp - m); e += 256) Ys[(e / (mp - m)) * ldq + m + e % (mp - m)] = 0.f;
         __syncthreads();
-        // this tile's share of Y^T Y (fixed summation order -> deterministic)
+        // this tile's Y^T Y on tensor cores, Y split into two tf32 terms (three
+        // products); each warp owns 16 x 8 output tiles in a fixed order
         float* Hp = sc.Hp + (size_t)tile * m * m;
-        const int nr = min(128, rows - r0);
-        for (int e = tid; e < m * m; e += 256) {
-            const int a = e / m, cc = e - (e / m) * m;
-            if (cc < a) continue;
-            float h0 = 0.f, h1 = 0.f;
-            int r = 0;
-            for (; r + 1 < nr; r += 2) {
-                h0 = fmaf(Ys[r * ldy + a], Ys[r * ldy + cc], h0);
-                h1 = fmaf(Ys[(r + 1) * ldy + a], Ys[(r + 1) * ldy + cc], h1);
+        const int nmt = mp / 16;
+        for (int ot = warp; ot < nmt * ntn; ot += 8) {
+            const int mt = ot / ntn, nt = ot - (ot / ntn) * ntn;
+            float h[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k0 = 0; k0 < 128; k0 += 8) {
+                const float* ya = Ys + (k0 + t4) * ldq + mt * 16 + g;
+                const float* yb = Ys + (k0 + t4) * ldq + nt * 8 + g;
+                uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3, bh0, bl0, bh1, bl1;
+                tf32_split(ya[0], ah0, al0);
+                tf32_split(ya[8], ah1, al1);
+                tf32_split(ya[4 * ldq], ah2, al2);
+                tf32_split(ya[4 * ldq + 8], ah3, al3);
+                tf32_split(yb[0], bh0, bl0);
+                tf32_split(yb[4 * ldq], bh1, bl1);
+                mma_tf32(h, al0, al1, al2, al3, bh0, bh1);
+                mma_tf32(h, ah0, ah1, ah2, ah3, bl0, bl1);
+                mma_tf32(h, ah0, ah1, ah2, ah3, bh0, bh1);
             }
-            if (r < nr) h0 = fmaf(Ys[r * ldy + a], Ys[r * ldy + cc], h0);
-            const float h = h0 + h1;
-            Hp[a * m + cc] = h;
-            Hp[cc * m + a] = h;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = mt * 16 + g + ((e >> 1) ? 8 : 0);
+                const int j = nt * 8 + 2 * t4 + (e & 1);
+                if (i < m) Hp[i * m + j] = h[e];
+            }
         }
     }
 }
@@ -502,14 +538,13 @@ __global__ void __launch_bounds__(256) k_project(Src src, TcScratch sc, int n) {
 // ---------------------------------------------------------------------------
 constexpr int kSketchCL = 4;
 
-// Random sign of Omega(i, c): the SplitMix64 output function (Steele, Lea &
-// Flood, OOPSLA 2014) of the counter (i, c).
-__device__ __forceinline__ float omega_sign(uint32_t i, uint32_t c) {
-    uint64_t z = (((uint64_t)i << 32) | c) + 0x9E3779B97F4A7C15ull;
+// Random signs of row i of Omega: bit c of the SplitMix64 output function
+// (Steele, Lea & Flood, OOPSLA 2014) of the counter i gives Omega(i, c), c < 64.
+__device__ __forceinline__ uint64_t omega_row_bits(uint32_t i) {
+    uint64_t z = (uint64_t)i + 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return (z & 1) ? 1.f : -1.f;
+    return z ^ (z >> 31);
 }
 
 // Shared-memory plan of k_sketch (bytes from the dynamic base):
@@ -563,9 +598,13 @@ __global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * 
                      ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
     const auto cx = src.ctx(item, sizeof(Tin));
 
-    for (int e = tid; e < npad * m; e += 256) {
-        const int l = e / m, c = e - (e / m) * m;
-        Bs[l * ldb + c] = __float2bfloat16_rn(l < n ? omega_sign((uint32_t)l, (uint32_t)c) : 0.f);
+    for (int l = tid; l < npad; l += 256) {
+        const uint64_t bits = omega_row_bits((uint32_t)l);
+        for (int c = 0; c < m; c += 2) {
+            const float a = l < n ? (((bits >> c) & 1) ? 1.f : -1.f) : 0.f;
+            const float b = l < n ? (((bits >> (c + 1)) & 1) ? 1.f : -1.f) : 0.f;
+            *reinterpret_cast<uint32_t*>(Bs + l * ldb + c) = pack_bf16(__float2bfloat16_rn(a), __float2bfloat16_rn(b));
+        }
     }
     float sacc[NMT][MB / 8][4];
 #pragma unroll
@@ -577,14 +616,27 @@ __global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * 
     for (int t = cr; t < ntl; t += kSketchCL) {
         const int r0 = t * 128;
         __syncthreads();
-        // X tile -> bf16 Xs (zero rows past `rows`, columns past n)
+        // X tile -> bf16 Xs (zero rows past `rows`, columns past n); element
+        // group f = tid + 256 j sits at row f / q4, column 4 (f % q4), advanced
+        // incrementally (no division in the loop)
         const int q4 = npad / 4;
+        const int dr = 256 / q4, dc = 256 - dr * q4;
+        int r_i = tid / q4, c_i = tid - r_i * q4;
         for (int f0 = 0; f0 < 128 * q4; f0 += 256 * 8) {
             float v[8][4];
+            int rs[8], cs[8];
+#pragma unroll
+            for (int gg = 0; gg < 8; ++gg) {
+                rs[gg] = r_i;
+                cs[gg] = c_i * 4;
+                r_i += dr;
+                c_i += dc;
+                if (c_i >= q4) { c_i -= q4; ++r_i; }
+            }
 #pragma unroll
             for (int gg = 0; gg < 8; ++gg) {
                 const int f = f0 + tid + gg * 256;
-                const int r = f / q4, c = (f - r * q4) * 4;
+                const int r = rs[gg], c = cs[gg];
                 v[gg][0] = v[gg][1] = v[gg][2] = v[gg][3] = 0.f;
                 if (f < 128 * q4 && r0 + r < rows) {
                     float s = 1.f;
@@ -609,7 +661,7 @@ __global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * 
             for (int gg = 0; gg < 8; ++gg) {
                 const int f = f0 + tid + gg * 256;
                 if (f >= 128 * q4) break;
-                const int r = f / q4, c = (f - r * q4) * 4;
+                const int r = rs[gg], c = cs[gg];
                 uint32_t* dp = reinterpret_cast<uint32_t*>(Xs + r * ldx + c);
                 dp[0] = pack_bf16(__float2bfloat16_rn(v[gg][0]), __float2bfloat16_rn(v[gg][1]));
                 dp[1] = pack_bf16(__float2bfloat16_rn(v[gg][2]), __float2bfloat16_rn(v[gg][3]));
@@ -730,45 +782,125 @@ __global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * 
 }
 
 // ---------------------------------------------------------------------------
-// 2''. Orthonormal basis of the sketch, one CTA per item: S (n x m, sc.G) ->
-//      two-pass Gram-Schmidt with replacement of dependent columns -> Q~
-//      rounded to tf32 (exact operand of the projection) and C = Q~^T Q~.
+// 2''. Orthonormal basis of the sketch, one CTA of 16 warps per item: warp w
+//      owns columns w, w + 16, ... of S (n x m, sc.G) with RPL rows per lane
+//      in registers.  Right-looking modified Gram-Schmidt: the owner
+//      normalises column c and publishes it, then every warp removes its
+//      component from its later columns (warp-shuffle dots).  One pass leaves
+//      Q~ orthonormal to ~eps kappa(S); the Rayleigh-Ritz step uses the exact
+//      Q~^T Q~, so only the conditioning of Q~ matters here.  A column whose
+//      norm falls below 1e-5 of its starting norm is dependent and becomes
+//      zero: its direction carries rounding error of order eps / 1e-5, and
+//      such directions (lambda_j < 1e-5 lambda_1) lie below what the fp32
+//      Gram route resolves anyway.  Q~ is rounded to tf32 (exact operand of the
+//      projection); C = Q~^T Q~ follows.
 // ---------------------------------------------------------------------------
-template <class Src>
-__global__ void __launch_bounds__(256) k_orth(Src src, TcScratch sc, int n) {
-    extern __shared__ __align__(16) float osm[];
-    __shared__ float red[32];
-    __shared__ float coef[ZS_MAXM];
-    const int m = sc.m, lds = m + 1, tid = threadIdx.x;
-    float* Q = osm;                                  // n x lds
-    for (int item = blockIdx.x; item < src.count(); item += gridDim.x) {
-        const float* Sg = sc.G + (size_t)item * n * m;
-        __syncthreads();
-        for (int e = tid; e < n * m; e += 256) Q[(e / m) * lds + (e % m)] = Sg[e];
-        __syncthreads();
-        mgs_orth<float>(Q, lds, n, m, red, coef);
-        float* Qf = sc.Qf + (size_t)item * n * m;
-        for (int e = tid; e < n * m; e += 256) {
-            const int l = e / m, c = e - (e / m) * m;
-            const float h = __uint_as_float(to_tf32(Q[l * lds + c]));
-            Qf[e] = h;
-            Q[l * lds + c] = h;                      // Q~ as it will be used
+constexpr int kOrthWarps = 16;
+
+template <class Src, int RPL, int CPW>
+__global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc, int n) {
+    extern __shared__ __align__(16) float osm[];     // Q~, n x (m+1), for C
+    __shared__ float qc[2 * 32 * RPL];                // the published column (two buffers)
+    const int m = sc.m, lds = m + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = blockIdx.x;
+    if (item >= src.count()) return;
+    const float* Sg = sc.G + (size_t)item * n * m;
+    float s[CPW][RPL], nrm0[CPW];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+        const int col = warp + kOrthWarps * j;
+        float ss = 0.f;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int row = lane + 32 * r;
+            s[j][r] = (col < m && row < n) ? Sg[(size_t)row * m + col] : 0.f;
+            ss = fmaf(s[j][r], s[j][r], ss);
+        }
+        nrm0[j] = sqrtf(warp_sum(ss));
+    }
+    // one pass; the published column alternates between two buffers so that a
+    // single barrier per column separates its writer from its readers
+    for (int c = 0; c < m; ++c) {
+        const int ow = c % kOrthWarps, oj = c / kOrthWarps;
+        float* qb = qc + (c & 1) * 32 * RPL;
+        if (warp == ow) {
+            float v[RPL];
+            float base = 0.f;
+#pragma unroll
+            for (int j = 0; j < CPW; ++j)
+                if (j == oj) {
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) v[r] = s[j][r];
+                    base = nrm0[j];
+                }
+            float ss = 0.f;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) ss = fmaf(v[r], v[r], ss);
+            const float nn = sqrtf(warp_sum(ss));
+            const float inv = (nn > 0.f && nn > 1e-5f * base) ? 1.f / nn : 0.f;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                v[r] *= inv;
+                qb[lane + 32 * r] = v[r];
+            }
+#pragma unroll
+            for (int j = 0; j < CPW; ++j)
+                if (j == oj) {
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) s[j][r] = v[r];
+                }
         }
         __syncthreads();
-        // C = Q~^T Q~ (exact products of tf32 values, fp32 sums)
-        float* Cq = sc.Cq + (size_t)item * m * m;
-        for (int e = tid; e < m * m; e += 256) {
-            const int a = e / m, c = e - (e / m) * m;
-            if (c < a) continue;
-            float h0 = 0.f, h1 = 0.f;
-            int i = 0;
-            for (; i + 1 < n; i += 2) {
-                h0 = fmaf(Q[i * lds + a], Q[i * lds + c], h0);
-                h1 = fmaf(Q[(i + 1) * lds + a], Q[(i + 1) * lds + c], h1);
+        float q[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) q[r] = qb[lane + 32 * r];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const int d = warp + kOrthWarps * j;
+            if (d > c && d < m) {
+                float dot = 0.f;
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) dot = fmaf(q[r], s[j][r], dot);
+                dot = warp_sum(dot);
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) s[j][r] = fmaf(-dot, q[r], s[j][r]);
             }
-            if (i < n) h0 = fmaf(Q[i * lds + a], Q[i * lds + c], h0);
-            Cq[a * m + c] = h0 + h1;
-            Cq[c * m + a] = h0 + h1;
+        }
+    }
+    // Q~ = tf32(Q): to the projection's scratch and, for C, to shared memory
+    float* Qf = sc.Qf + (size_t)item * n * m;
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+        const int col = warp + kOrthWarps * j;
+        if (col >= m) continue;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int row = lane + 32 * r;
+            s[j][r] = __uint_as_float(to_tf32(s[j][r]));
+            if (row < n) {
+                Qf[(size_t)row * m + col] = s[j][r];
+                osm[row * lds + col] = s[j][r];
+            }
+        }
+    }
+    __syncthreads();
+    // C = Q~^T Q~ (exact products of tf32 values, fp32 sums; the same
+    // summation tree for C[a][c] and C[c][a], so C is exactly symmetric)
+    float* Cq = sc.Cq + (size_t)item * m * m;
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+        const int a = warp + kOrthWarps * j;
+        if (a >= m) continue;
+        for (int c = 0; c < m; ++c) {
+            float dot = 0.f;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int row = lane + 32 * r;
+                if (row < n) dot = fmaf(s[j][r], osm[row * lds + c], dot);
+            }
+            dot = warp_sum(dot);
+            if (lane == 0) Cq[a * m + c] = dot;
         }
     }
 }
@@ -937,58 +1069,83 @@ __device__ __forceinline__ int rr_partner32(int x, int r) {
     return y == x ? 0 : y;
 }
 
-// In-register Cholesky of the warp's symmetric 32 x 32 matrix (lane l holds
-// column l).  On return lane l holds column l of L (zeros above the
-// diagonal); a pivot <= 0 gives a zero column.
-__device__ __forceinline__ void warp_chol32(float (&a)[32], int lane) {
-#pragma unroll
+// The loops below run over the pivot index without unrolling (the code stays
+// small); the lane's vector is shifted down one register per step so that
+// the pivot element is always register 0 and every index stays static.
+
+// Cholesky A = L L^T of the warp's symmetric 32 x 32 matrix held as column
+// `lane` in a[].  L goes to the per-warp tile T (row-major, stride 33); on
+// return a[] holds column `lane` of L.  A pivot <= 0 gives a zero column.
+__device__ __forceinline__ void warp_chol32(float (&a)[32], float* T, int lane) {
     for (int j = 0; j < 32; ++j) {
-        const float piv = __shfl_sync(0xffffffffu, a[j], j);
+        // a[0..31-j] hold rows j.. of column `lane`
+        const float piv = __shfl_sync(0xffffffffu, a[0], j);
         const float d = piv > 0.f ? sqrtf(piv) : 0.f;
         const float inv = d > 0.f ? 1.f / d : 0.f;
-        const float slj = a[j] * inv;                       // L[lane][j] for lane > j
+        const float slj = a[0] * inv;                       // L[lane][j] for lane > j
+        if (lane == j) T[j * 33 + j] = d;
 #pragma unroll
-        for (int i = j + 1; i < 32; ++i) {
-            const float lij = __shfl_sync(0xffffffffu, a[i], j) * inv;
+        for (int i = 1; i < 32; ++i) {
+            const float lij = __shfl_sync(0xffffffffu, a[i], j) * inv;   // L[j+i][j]
+            if (lane == j && j + i < 32) T[(j + i) * 33 + j] = lij;
             if (lane > j) a[i] = fmaf(-lij, slj, a[i]);
         }
-        if (lane == j) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) a[i] = i < j ? 0.f : (i == j ? d : a[i] * inv);
-        }
+        for (int i = 0; i < 31; ++i) a[i] = a[i + 1];
+        a[31] = 0.f;
     }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) a[i] = i >= lane ? T[i * 33 + lane] : 0.f;
+    __syncwarp();
 }
 
-// x = L^-1 h for every lane's own vector h (L: lane p holds column p).
-__device__ __forceinline__ void warp_fsub32(const float (&L)[32], const float (&h)[32], float (&x)[32]) {
+// x = L^-1 h for every lane's own vector h (L row-major in T, stride 33).
+// The solution is also left in W as W[i][lane] (row-major, stride 33).
+__device__ __forceinline__ void warp_fsub32(const float* T, float (&h)[32], float (&x)[32], float* W, int lane) {
+    for (int p = 0; p < 32; ++p) {
+        const float dpp = T[p * 33 + p];
+        const float xp = dpp > 0.f ? h[0] / dpp : 0.f;
+        W[p * 33 + lane] = xp;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        float acc = h[i];
+        for (int i = 1; i < 32; ++i)
+            if (p + i < 32) h[i] = fmaf(-T[(p + i) * 33 + p], xp, h[i]);
 #pragma unroll
-        for (int p = 0; p < i; ++p) acc = fmaf(-__shfl_sync(0xffffffffu, L[i], p), x[p], acc);
-        const float dii = __shfl_sync(0xffffffffu, L[i], i);
-        x[i] = dii > 0.f ? acc / dii : 0.f;
+        for (int i = 0; i < 31; ++i) h[i] = h[i + 1];
+        h[31] = 0.f;
     }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = W[i * 33 + lane];
 }
 
-// z = L^-T w for every lane's own vector w.
-__device__ __forceinline__ void warp_bsub32(const float (&L)[32], const float (&w)[32], float (&z)[32]) {
-#pragma unroll
+// z = L^-T w for every lane's own vector w (L row-major in T); W as above.
+__device__ __forceinline__ void warp_bsub32(const float* T, float (&w)[32], float (&z)[32], float* W, int lane) {
     for (int i = 31; i >= 0; --i) {
-        float acc = w[i];
+        // w[31 - q] holds w_{i - q}
+        const float dii = T[i * 33 + i];
+        const float zi = dii > 0.f ? w[31] / dii : 0.f;
+        W[i * 33 + lane] = zi;
 #pragma unroll
-        for (int p = i + 1; p < 32; ++p) acc = fmaf(-__shfl_sync(0xffffffffu, L[p], i), z[p], acc);
-        const float dii = __shfl_sync(0xffffffffu, L[i], i);
-        z[i] = dii > 0.f ? acc / dii : 0.f;
+        for (int q = 1; q < 32; ++q)
+            if (q <= i) w[31 - q] = fmaf(-T[i * 33 + (i - q)], zi, w[31 - q]);
+#pragma unroll
+        for (int q = 31; q > 0; --q) w[q] = w[q - 1];
+        w[0] = 0.f;
     }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = W[i * 33 + lane];
 }
 
 template <class Src>
 __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int kw) {
-    __shared__ float tr[4][32 * 33];                  // per-warp transpose buffer
+    __shared__ float tl[4][32 * 33];                  // per warp: Cholesky factor of C
+    __shared__ float tw[4][32 * 33];                  // per warp: work tile
     const int m = sc.m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    float* T = tr[warp];
+    float* TL = tl[warp];
+    float* TW = tw[warp];
     // one item per warp (the launch covers every item): the register arrays
     // below stay in registers only while no loop encloses the unrolled code
     const int item = blockIdx.x * wpc + warp;
@@ -1011,39 +1168,40 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
             for (int i = 0; i < 32; ++i)
                 if (i < m && lane < m) v[i] += hp[i * m + lane];
         }
-        warp_chol32(lc, lane);
-        warp_fsub32(lc, v, x);                         // X = L^-1 H, column `lane`
-        __syncwarp();
+        warp_chol32(lc, TL, lane);                     // C = L L^T, L in TL
+        warp_fsub32(TL, v, x, TW, lane);               // X = L^-1 H, column `lane` (also in TW)
 #pragma unroll
-        for (int i = 0; i < 32; ++i) T[i * 33 + lane] = x[i];
+        for (int i = 0; i < 32; ++i) v[i] = TW[lane * 33 + i];   // row `lane` of X
         __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = T[lane * 33 + i];   // row `lane` of X
-        warp_fsub32(lc, v, x);                         // H' = L^-1 X^T, column `lane`
-        warp_chol32(x, lane);                          // H' = G G^T, column `lane` of G
+        warp_fsub32(TL, v, x, TW, lane);               // H' = L^-1 X^T, column `lane`
+        __syncwarp();
+        warp_chol32(x, TW, lane);                      // H' = G G^T, column `lane` of G
         // one-sided Jacobi on the columns of G
         float al = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
-        const float tol = 4.f * 1.1920929e-7f;
+        // converged when every pair is orthogonal to the rounding level of a
+        // 32-term fp32 dot product (m eps): a tighter test never stops rotating
+        const float tol = 32.f * 1.1920929e-7f;
         for (int sweep = 0; sweep < 30; ++sweep) {
             int rotated = 0;
             for (int r = 0; r < 31; ++r) {
                 const int pr = rr_partner32(lane, r);
                 const bool isp = lane < pr;
-                float g = 0.f;
+                float g4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     v[i] = __shfl_sync(0xffffffffu, x[i], pr);
-                    g = fmaf(x[i], v[i], g);
+                    g4[i & 3] = fmaf(x[i], v[i], g4[i & 3]);
                 }
+                const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
                 const float ao = __shfl_sync(0xffffffffu, al, pr);
                 const float app = isp ? al : ao, aqq = isp ? ao : al;
                 float c = 1.f, s = 0.f;
                 if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
                     const float zeta = (aqq - app) / (2.f * g);
-                    const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    c = 1.f / sqrtf(1.f + t * t);
+                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                    c = 1.f / sqrtf(fmaf(t, t, 1.f));
                     s = c * t;
                     al = isp ? app - t * g : aqq + t * g;
                     rotated = 1;
@@ -1075,7 +1233,8 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
             const float ot = __shfl_sync(0xffffffffu, al, o);
             rk += (ot > al) || (ot == al && o < lane);
         }
-        warp_bsub32(lc, x, v);                         // z = L^-T w
+        __syncwarp();
+        warp_bsub32(TL, x, v, TW, lane);               // z = L^-T w
         if (rk < kw) {
             float* Zg = sc.Zs + (size_t)item * m * kw;
 #pragma unroll
@@ -1089,22 +1248,73 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
 // ---------------------------------------------------------------------------
 // 4b. Outputs per item: sigma = sqrt(theta), V = Q~ Z (signed), U = Y Z Sigma^-1.
 // ---------------------------------------------------------------------------
+// Shared-memory plan of k_rr_out: Z (m x ldz) then V (n x (kwp + 1)), with
+// kwp = kw rounded up to 8 and ldz = 8 mod 32 (conflict-free B fragments).
+__host__ __device__ __forceinline__ int rro_kwp(int kw) { return (kw + 7) / 8 * 8; }
+__host__ __device__ __forceinline__ int rro_ldz(int kw) { return (rro_kwp(kw) + 31) / 32 * 32 + 8; }
+__host__ __device__ __forceinline__ size_t rr_out_smem_bytes(int n, int m, int kw) {
+    return sizeof(float) * ((size_t)m * rro_ldz(kw) + (size_t)n * (rro_kwp(kw) + 1));
+}
+
+// D(16 x kwp rows r0..) = A(rows x m, global fp32, row stride m) . Zs(m x kwp)
+// on tf32 tensor cores; A_EXACT: A is already tf32 (one product), else A and
+// Z are split into two terms each (three products).  Rows >= nrows read as 0.
+template <bool A_EXACT>
+__device__ __forceinline__ void rro_tile(const float* A, int r0, int nrows, int m, const float* Zs, int ldz,
+                                         int nnt, float (&acc)[8][4], int lane) {
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const int ra = r0 + g, rb = r0 + g + 8;
+    const float* pa = A + (size_t)ra * m;
+    const float* pb = A + (size_t)rb * m;
+    for (int k0 = 0; k0 < m; k0 += 8) {
+        const float x0 = ra < nrows ? __ldg(pa + k0 + t4) : 0.f;
+        const float x1 = rb < nrows ? __ldg(pb + k0 + t4) : 0.f;
+        const float x2 = ra < nrows ? __ldg(pa + k0 + t4 + 4) : 0.f;
+        const float x3 = rb < nrows ? __ldg(pb + k0 + t4 + 4) : 0.f;
+        uint32_t h0, h1, h2, h3, l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+        if constexpr (A_EXACT) {
+            h0 = __float_as_uint(x0); h1 = __float_as_uint(x1); h2 = __float_as_uint(x2); h3 = __float_as_uint(x3);
+        } else {
+            tf32_split(x0, h0, l0); tf32_split(x1, h1, l1); tf32_split(x2, h2, l2); tf32_split(x3, h3, l3);
+        }
+        const float* zb = Zs + (k0 + t4) * ldz + g;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            if (nt >= nnt) break;
+            uint32_t bh0, bl0, bh1, bl1;
+            tf32_split(zb[nt * 8], bh0, bl0);
+            tf32_split(zb[4 * ldz + nt * 8], bh1, bl1);
+            if constexpr (!A_EXACT) mma_tf32(acc[nt], l0, l1, l2, l3, bh0, bh1);
+            mma_tf32(acc[nt], h0, h1, h2, h3, bl0, bl1);
+            mma_tf32(acc[nt], h0, h1, h2, h3, bh0, bh1);
+        }
+    }
+}
+
 template <class Src, bool QUERY>
 __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, int kw) {
     extern __shared__ __align__(16) char dsm[];
-    const int m = sc.m;
-    float* Zsm = (float*)dsm;                  // m x kw
-    float* Vs = Zsm + (size_t)m * kw;          // n x kw
+    const int m = sc.m, kwp = rro_kwp(kw), ldz = rro_ldz(kw), ldv = kwp + 1, nnt = kwp / 8;
+    float* Zsm = (float*)dsm;                  // m x ldz
+    float* Vs = Zsm + (size_t)m * ldz;         // n x ldv
     __shared__ float sig[ZS_MAXM];
     __shared__ float sgnf[ZS_MAXM];
     __shared__ int s_rank;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
     for (int item = blockIdx.x; item < src.count(); item += gridDim.x) {
         const int rows = src.rows(item);
         const float* Y = sc.Y + (size_t)src.ybase(item) * m;
         const float* Qf = sc.Qf + (size_t)item * n * m;
         __syncthreads();
-        for (int e = tid; e < m * kw; e += nt) Zsm[e] = sc.Zs[(size_t)item * m * kw + e];
+        for (int e = tid; e < m * kwp; e += nt) {
+            const int a = e / kwp, c = e - (e / kwp) * kwp;
+            Zsm[a * ldz + c] = c < kw ? sc.Zs[(size_t)item * m * kw + a * kw + c] : 0.f;
+        }
         int kcap;
         if constexpr (QUERY) kcap = src.a.plans[item].kcap;
         else kcap = min(kw, min(rows, n));
@@ -1117,20 +1327,26 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
             sig[c] = sv;
             if (sv > 0.f) atomicAdd(&s_rank, 1);
         }
-        // V = Q~ Z
-        for (int e = tid; e < n * kw; e += nt) {
-            const int l = e / kw, c = e - (e / kw) * kw;
-            float v = 0.f;
-            const float* qr = Qf + (size_t)l * m;
-            for (int a = 0; a < m; ++a) v += qr[a] * Zsm[a * kw + c];
-            Vs[e] = v;
+        // V = Q~ Z on tensor cores (Q~ exact in tf32), 16-row tiles per warp
+        for (int rt = wid; rt * 16 < n; rt += nw) {
+            float acc[8][4];
+            rro_tile<true>(Qf, rt * 16, n, m, Zsm, ldz, nnt, acc, lane);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nnt) break;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int l = rt * 16 + g + ((e >> 1) ? 8 : 0), c = q * 8 + 2 * t4 + (e & 1);
+                    if (l < n) Vs[l * ldv + c] = acc[q][e];
+                }
+            }
         }
         __syncthreads();
         for (int c = wid; c < kw; c += nw) {
             float best = -1.f;
             int bi = 0x7fffffff;
             for (int l = lane; l < n; l += 32) {
-                const float av = fabsf(Vs[l * kw + c]);
+                const float av = fabsf(Vs[l * ldv + c]);
                 if (av > best || (av == best && l < bi)) { best = av; bi = l; }
             }
 #pragma unroll
@@ -1139,7 +1355,7 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
-            if (lane == 0) sgnf[c] = (bi < n && Vs[bi * kw + c] < 0.f) ? -1.f : 1.f;
+            if (lane == 0) sgnf[c] = (bi < n && Vs[bi * ldv + c] < 0.f) ? -1.f : 1.f;
         }
         __syncthreads();
         float* vt_out;
@@ -1159,7 +1375,7 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
             if (tid == 0 && P.rank) *P.rank = s_rank;
             for (int e = tid; e < n * src.a.kout; e += nt) {
                 const int l = e / src.a.kout, c = e - (e / src.a.kout) * src.a.kout;
-                const float v = (c < kw && sig[c] > 0.f) ? sgnf[c] * Vs[l * kw + c] : 0.f;
+                const float v = (c < kw && sig[c] > 0.f) ? sgnf[c] * Vs[l * ldv + c] : 0.f;
                 ((float*)P.V_out)[(size_t)l * P.ldv + c] = v;
             }
         } else {
@@ -1172,37 +1388,36 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
         }
         for (int e = tid; e < kw * n; e += nt) {
             const int c = e / n, l = e - (e / n) * n;
-            vt_out[e] = sig[c] > 0.f ? sgnf[c] * Vs[l * kw + c] : 0.f;
+            vt_out[e] = sig[c] > 0.f ? sgnf[c] * Vs[l * ldv + c] : 0.f;
         }
         // fold sign / sigma into Z so that U = Y Zsm
         __syncthreads();
-        for (int e = tid; e < m * kw; e += nt) {
-            const int c = e % kw;
-            Zsm[e] = sig[c] > 0.f ? Zsm[e] * sgnf[c] / sig[c] : 0.f;
+        for (int e = tid; e < m * kwp; e += nt) {
+            const int a = e / kwp, c = e - (e / kwp) * kwp;
+            float& z = Zsm[a * ldz + c];
+            z = (c < kw && sig[c] > 0.f) ? z * sgnf[c] / sig[c] : 0.f;
         }
         __syncthreads();
-        for (int r = tid; r < urows; r += nt) {
-            float yr[ZS_MAXM];
-            if (r < rows) {
-                const float4* y4 = reinterpret_cast<const float4*>(Y + (size_t)r * m);
+        // U = Y Zsm on tensor cores (both split), 16-row tiles per warp
+        const bool pair = (kw % 2) == 0;
+        for (int rt = wid; rt * 16 < urows; rt += nw) {
+            float acc[8][4];
+            rro_tile<false>(Y, rt * 16, rows, m, Zsm, ldz, nnt, acc, lane);
 #pragma unroll
-                for (int a4 = 0; a4 < ZS_MAXM / 4; ++a4) {
-                    if (a4 * 4 >= m) break;
-                    const float4 v = __ldg(y4 + a4);
-                    yr[4 * a4] = v.x; yr[4 * a4 + 1] = v.y; yr[4 * a4 + 2] = v.z; yr[4 * a4 + 3] = v.w;
-                }
-            }
-            float* ur = u_out + (size_t)r * kw;
-            for (int c = 0; c < kw; ++c) {
-                float acc = 0.f;
-                if (r < rows) {
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nnt) break;
 #pragma unroll
-                    for (int a = 0; a < ZS_MAXM; ++a) {
-                        if (a >= m) break;
-                        acc += yr[a] * Zsm[a * kw + c];
+                for (int h = 0; h < 2; ++h) {
+                    const int r = rt * 16 + g + 8 * h, c = q * 8 + 2 * t4;
+                    if (r >= urows || c >= kw) continue;
+                    float* up = u_out + (size_t)r * kw + c;
+                    if (pair) {
+                        *reinterpret_cast<float2*>(up) = make_float2(acc[q][2 * h], acc[q][2 * h + 1]);
+                    } else {
+                        up[0] = acc[q][2 * h];
+                        if (c + 1 < kw) up[1] = acc[q][2 * h + 1];
                     }
                 }
-                ur[c] = acc;
             }
         }
     }
