@@ -200,16 +200,35 @@ def run_reference(args, w):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-def kernel_model(name, w, launches_per_step, nq_total_rows):
-    """Algorithmic work per launch of a kernel, for the roofline object."""
+def union_rows(ts, te):
+    """Rows covered by at least one of the inclusive ranges [ts_i, te_i]."""
+    order = np.argsort(ts)
+    total, cur_lo, cur_hi = 0, None, None
+    for i in order:
+        a, z = int(ts[i]), int(te[i])
+        if cur_hi is None or a > cur_hi + 1:
+            if cur_hi is not None:
+                total += cur_hi - cur_lo + 1
+            cur_lo, cur_hi = a, z
+        else:
+            cur_hi = max(cur_hi, z)
+    if cur_hi is not None:
+        total += cur_hi - cur_lo + 1
+    return total
+
+
+def kernel_model(name, w, launches_per_step, nq_total_rows, union_u_rows):
+    """Compulsory bytes per launch of a kernel, for the roofline object."""
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
     T, n, b, k = w.series.T, w.series.n, w.b, w.k
-    if name in ("gram_compress", "form_u", "gram_lo", "project"):
+    if name in ("gram_compress", "form_u", "gram_lo", "project", "sketch"):
         # every input byte read once per launch set
         return "hbm", T * n * itemsize / launches_per_step
     if name == "lift":
-        # read U rows (k) and write output rows (k_out = k), factor type 4 B
-        return "hbm", nq_total_rows * 2 * k * 4 / launches_per_step
+        # write every output row (k_out = k floats); read each stored U row
+        # that the batch touches once (rows shared by several queries come
+        # from L2 after the first read)
+        return "hbm", (nq_total_rows * k * 4 + union_u_rows * k * 4) / launches_per_step
     return None, None
 
 
@@ -315,7 +334,7 @@ def run_gpu(args, w):
     if dom:
         name, (nl, ms) = dom
         per_step = nl / K
-        bound, units = kernel_model(name, w, per_step, out_rows)
+        bound, units = kernel_model(name, w, per_step, out_rows, union_rows(ts, te))
         avg_s = ms / nl / 1e3
         if bound == "hbm":
             ach = units / avg_s / 1e9
@@ -330,6 +349,12 @@ def run_gpu(args, w):
     acc = None
     if rank == 0 and not args.skip_accuracy and nq:
         acc = accuracy_sample(st, w, A)
+    plain = None
+    if rank == 0 and not args.skip_plain and nq:
+        st.close()
+        del rows_dev
+        torch.cuda.empty_cache()
+        plain = plain_fp64_run(w, A, ts, te, local)
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = serve_run(args.serve_seconds, local)
@@ -351,13 +376,66 @@ def run_gpu(args, w):
                            "parallelism": f"replicas x{ws}"},
                 "queries_per_s": qps, "compress_s_per_step": tc / K, "query_s_per_step": tq / K,
                 "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"],
-                "accuracy": acc, "serving": serving,
+                "accuracy": acc, "serving": serving, "plain_fp64_gpu": plain,
+                "queries_per_s_vs_plain": (qps / plain["queries_per_s"]) if (plain and qps) else None,
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
-    st.close()
+    if plain is None:
+        st.close()
     if dist:
         dist.destroy_process_group()
+
+
+def plain_fp64_run(w, A, ts, te, local, budget_s=4.0, acc_queries=3):
+    """The same range-SVD method as a plain FP64 GPU program, one query at a
+    time: an FP64 store of the same rows (FP64 CUDA-core kernels throughout),
+    each query answered by its own zs_query call and synchronised before the
+    next - no batching, no mixed precision.  Queries are taken in the batch's
+    order until budget_s has passed."""
+    import oracle
+    import torch
+    import paper_1805_00754_gb300 as zs
+    T, n, b, k = w.series.T, w.series.n, w.b, w.k
+    if w.dtype == "bf16":
+        A64 = synthetic.bf16_bits_to_f64(np.asarray(A).view(np.uint16))
+    else:
+        A64 = np.asarray(A, dtype=np.float64)
+    dev = torch.from_numpy(A64).to(f"cuda:{local}")
+    st = zs.Store(n=n, b=b, k=k, dtype="f64", capacity_rows=T, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.append(dev)
+    torch.cuda.synchronize()
+    tc = time.perf_counter() - t0
+    del dev
+    lmax = int(np.max(te - ts + 1))
+    out = st.new_result(0, lmax - 1, k)
+    st.query(int(ts[0]), int(te[0]), out=out)            # warm-up (first launch, plan buffers)
+    torch.cuda.synchronize()
+    nq, t1 = 0, time.perf_counter()
+    while nq < len(ts) and time.perf_counter() - t1 < budget_s:
+        st.query(int(ts[nq]), int(te[nq]), out=out)
+        torch.cuda.synchronize()
+        nq += 1
+    tq = time.perf_counter() - t1
+    # accuracy of a few short ranges against the oracle, as for the batched form
+    worst = 0.0
+    qa, qz = synthetic.queries(T, acc_queries, 2 * b, 20_000, seed=7)
+    for a, z in zip(qa, qz):
+        S, E = int(a) // b, int(z) // b
+        ost = oracle.compress(A64[S * b: min((E + 1) * b, T)], b, k)
+        ref = oracle.query(ost, int(a) - S * b, int(z) - S * b)
+        o = st.query(int(a), int(z))
+        torch.cuda.synchronize()
+        s_ = o.S.cpu().numpy()
+        msk = ref.s > 0
+        worst = max(worst, float(np.max(np.abs(s_[msk] - ref.s[msk]) / ref.s[msk])))
+    st.close()
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    return {"form": "FP64 store and kernels, one zs_query call per query, synchronised", "queries": nq,
+            "queries_per_s": nq / max(tq, 1e-9), "compress_s": tc,
+            "compress_gbps_of_input": T * n * itemsize / tc / 1e9, "sigma_max_rel_err": worst}
 
 
 def accuracy_sample(st, w, A, nq=4, max_len=20_000, seed=7):
@@ -479,6 +557,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=6.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true", help="skip the one-query-at-a-time FP64 GPU form")
     ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")
     args = ap.parse_args()
     w = synthetic.WORKLOADS[args.workload]

@@ -354,6 +354,24 @@ static zs_status store_alloc(zs_store* st) {
     ZS_CU(cudaMemset(st->sig, 0, ts * nb * c.k), "memset");
     ZS_CU(cudaMemset(st->vt, 0, ts * nb * c.k * c.n), "memset");
     ZS_CU(cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking), "stream");
+    // chunk pipeline (tensor path with the sketch kernel: no shared per-CTA workspace)
+    if (use_tc_path(st->fp64, (int)c.n, c.flags) &&
+        tc_sketch_path((int)c.n, tc_width(c.k, st->tune.eig_m_extra), st->tune.fused_sketch) && st->gchunk >= 2 &&
+        st->tune.pipe_sub_blocks > 0) {
+        const int m = tc_width(c.k, st->tune.eig_m_extra);
+        const int sub = std::min(st->gchunk / 2, st->tune.pipe_sub_blocks);
+        const int64_t tpb = (c.b + 127) / 128;
+        const size_t region = (tc_aux_bytes(sub, (int64_t)sub * tpb, m, c.k) + 255) & ~(size_t)255;
+        if (2 * region <= tc_aux_bytes(st->gchunk, (int64_t)st->gchunk * tpb, m, c.k)) {
+            st->sub_blocks = sub;
+            st->aux_region = region;
+            for (int i = 0; i < 2; ++i) {
+                ZS_CU(cudaStreamCreateWithFlags(&st->cstream[i], cudaStreamNonBlocking), "stream");
+                ZS_CU(cudaEventCreateWithFlags(&st->cjoin[i], cudaEventDisableTiming), "event");
+            }
+            ZS_CU(cudaEventCreateWithFlags(&st->cfork, cudaEventDisableTiming), "event");
+        }
+    }
     for (int i = 0; i < 2; ++i) {
         ZS_CU(cudaEventCreateWithFlags(&st->stage_free[i], cudaEventDisableTiming), "event");
         ZS_CU(cudaEventCreateWithFlags(&st->stage_full[i], cudaEventDisableTiming), "event");
@@ -406,6 +424,8 @@ extern "C" void zs_store_destroy(zs_store* st) {
     if (!st) return;
     DeviceGuard g(st->cfg.device);
     if (st->copy_stream) cudaStreamSynchronize(st->copy_stream);
+    for (int i = 0; i < 2; ++i)
+        if (st->cstream[i]) cudaStreamSynchronize(st->cstream[i]);
     cudaDeviceSynchronize();
     st->qx.release();
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
@@ -427,6 +447,11 @@ extern "C" void zs_store_destroy(zs_store* st) {
     if (st->append_done) cudaEventDestroy(st->append_done);
     if (st->entry) cudaEventDestroy(st->entry);
     if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
+    for (int i = 0; i < 2; ++i) {
+        if (st->cstream[i]) cudaStreamDestroy(st->cstream[i]);
+        if (st->cjoin[i]) cudaEventDestroy(st->cjoin[i]);
+    }
+    if (st->cfork) cudaEventDestroy(st->cfork);
     delete st;
 }
 
@@ -436,6 +461,46 @@ extern "C" void zs_store_destroy(zs_store* st) {
 static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64_t rows_total, int nblk,
                                  int64_t slot0, cudaStream_t stream, const zs_store::PipeSlot* ps = nullptr) {
     const zs_store_config& c = st->cfg;
+    if (!ps && st->sub_blocks > 0 && nblk > st->sub_blocks) {
+        // two-stream chunk pipeline: sub-chunk i runs on stream i % 2 with half
+        // i % 2 of the scratch; both streams join back into `stream`
+        const int sub = st->sub_blocks;
+        const int m = tc_width(c.k, st->tune.eig_m_extra);
+        ZS_CU(cudaEventRecord(st->cfork, stream), "event");
+        for (int i = 0; i < 2; ++i) ZS_CU(cudaStreamWaitEvent(st->cstream[i], st->cfork, 0), "wait");
+        int i = 0;
+        for (int j0 = 0; j0 < nblk; j0 += sub, ++i) {
+            const int r = i & 1;
+            const int nb = std::min(sub, nblk - j0);
+            CompressChunk ch;
+            memset(&ch, 0, sizeof ch);
+            ch.A = (const char*)A + (size_t)j0 * c.b * lda * st->insize;
+            ch.lda = lda;
+            ch.rows_total = std::min<int64_t>(rows_total - (int64_t)j0 * c.b, (int64_t)nb * c.b);
+            ch.nblk = nb;
+            ch.slot0 = (int32_t)(slot0 + j0);
+            ch.b = (int32_t)c.b;
+            ch.n = (int32_t)c.n;
+            ch.k = c.k;
+            ch.in_kind = c.in_dtype;
+            ch.G = (char*)st->gscr + (size_t)r * sub * st->tsize * c.n * c.n;
+            ch.U = st->U;
+            ch.sig = st->sig;
+            ch.vt = st->vt;
+            ch.ews = st->ews;
+            ch.ews_ctas = st->ews_ctas;
+            ch.qb = (char*)st->qb + (size_t)r * sub * 4 * m * c.n;
+            ch.ys = (char*)st->ys + (size_t)r * sub * 4 * m * c.b;
+            ch.aux = (char*)st->aux + (size_t)r * st->aux_region;
+            cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, st->cstream[r]);
+            if (e != cudaSuccess) return cuda_fail(e, "compression kernels");
+        }
+        for (int q = 0; q < 2; ++q) {
+            ZS_CU(cudaEventRecord(st->cjoin[q], st->cstream[q]), "event");
+            ZS_CU(cudaStreamWaitEvent(stream, st->cjoin[q], 0), "wait");
+        }
+        return ZS_OK;
+    }
     const int chunk = ps ? 1 : st->gchunk;
     for (int j0 = 0; j0 < nblk; j0 += chunk) {
         const int nb = std::min(chunk, nblk - j0);

@@ -99,6 +99,15 @@ struct zs_store {
         void *G = nullptr, *qb = nullptr, *ys = nullptr, *aux = nullptr, *ews = nullptr;
     } pipe[kPipe];
     int pipe_next = 0;
+    // chunk pipeline of large device appends on the tensor path: sub-chunks of
+    // `sub_blocks` blocks alternate between two streams, each with its own half
+    // of the chunk scratch, so that one sub-chunk's latency-bound kernels
+    // overlap the next one's streaming passes
+    cudaStream_t cstream[2] = {nullptr, nullptr};
+    cudaEvent_t cfork = nullptr;
+    cudaEvent_t cjoin[2] = {nullptr, nullptr};
+    int sub_blocks = 0;             // 0: no chunk pipeline
+    size_t aux_region = 0;          // bytes of Rayleigh-Ritz scratch per half
     std::mutex mu;
     zs::Tuning tune;
     zs::QueryExec qx;

@@ -22,6 +22,8 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
                                                  tu, st);
 }
 
+bool tc_sketch_path(int n, int m, int fused_sketch) { return fused_sketch && sketch_fits(n, m); }
+
 cudaError_t launch_compress_tc(const CompressChunk& c, int flags, const Tuning& tu, int num_sms, cudaStream_t st) {
     const bool ref = (flags & 1) != 0;
     if (c.in_kind == IN_BF16)

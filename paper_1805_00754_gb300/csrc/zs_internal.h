@@ -116,6 +116,7 @@ struct Tuning {
     int power_its = 1;           // tensor path: power steps on the bf16 Gram
     int project_ctas_per_sm = 8; // persistent grid of the projection kernel
     int fused_sketch = 1;        // tensor path: sketch kernel (else the bf16 Gram) where it fits
+    int pipe_sub_blocks = 0;     // tensor path: blocks per sub-chunk of the two-stream append pipeline (0: off)
 };
 
 // The tensor-core path (bf16 Gram for the subspace, split-bf16 projection and
@@ -149,6 +150,9 @@ EigPlan eig_plan(int n, int kq, int extra, bool fp64, bool refine);
 size_t eig_smem_bytes(int n, int m, bool fp64, bool refine, bool yglob);
 size_t eig_ws_bytes(int n, bool fp64, int ctas);
 size_t tc_aux_bytes(int64_t items, int64_t tiles, int m, int kw);
+// the tensor path takes the sketch kernels (no shared per-CTA workspace) for
+// this n and subspace width m
+bool tc_sketch_path(int n, int m, int fused_sketch);
 void note_launches(int64_t n);
 void profile_enable(int on);
 void profile_reset();

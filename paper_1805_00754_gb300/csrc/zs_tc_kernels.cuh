@@ -1180,10 +1180,11 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
         float al = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
-        // converged when every pair is orthogonal to the rounding level of a
-        // 32-term fp32 dot product (m eps): a tighter test never stops rotating
-        const float tol = 32.f * 1.1920929e-7f;
-        for (int sweep = 0; sweep < 30; ++sweep) {
+        // converged when every pair is orthogonal to 1e-5: safely above the
+        // rounding level of a 32-term fp32 dot product, which a tighter test
+        // could keep rotating at
+        const float tol = 1e-5f;
+        for (int sweep = 0; sweep < 15; ++sweep) {
             int rotated = 0;
             for (int r = 0; r < 31; ++r) {
                 const int pr = rr_partner32(lane, r);
@@ -1199,20 +1200,24 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
                 const float app = isp ? al : ao, aqq = isp ? ao : al;
                 float c = 1.f, s = 0.f;
                 if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
-                    const float zeta = (aqq - app) / (2.f * g);
-                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                    c = 1.f / sqrtf(fmaf(t, t, 1.f));
-                    s = c * t;
+                    // zeta and t need only be near the optimum (the sweep
+                    // repeats); c gets a Newton step so that c^2 + s^2 = 1 to
+                    // rounding and the column norms do not drift
+                    const float zeta = __fdividef(aqq - app, 2.f * g);
+                    const float r1 = fmaf(zeta, zeta, 1.f);
+                    const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + r1 * rsqrtf(r1));
+                    const float u = fmaf(t, t, 1.f);
+                    float cc = rsqrtf(u);
+                    cc = cc * fmaf(-0.5f * u * cc, cc, 1.5f);
+                    c = cc;
+                    s = cc * t;
                     al = isp ? app - t * g : aqq + t * g;
                     rotated = 1;
                 }
-                if (isp) {
+                // p: c x_p - s x_q; q: s x_p + c x_q (branch-free across the pair)
+                const float sv = isp ? -s : s;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) x[i] = c * x[i] - s * v[i];
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) x[i] = s * v[i] + c * x[i];
-                }
+                for (int i = 0; i < 32; ++i) x[i] = fmaf(sv, v[i], c * x[i]);
             }
             if (!__any_sync(0xffffffffu, rotated)) break;
             al = 0.f;

@@ -1,0 +1,30 @@
+"""Host-side arithmetic of bench.py's roofline and rate reporting (no GPU)."""
+import numpy as np
+
+import bench
+
+
+def test_union_rows_merges_overlapping_and_adjacent_ranges():
+    ts = np.array([20, 0, 5, 3, 11])
+    te = np.array([25, 4, 10, 6, 11])
+    # [0..11] (0-4, 3-6, 5-10 overlap; 11 is adjacent) and [20..25]
+    assert bench.union_rows(ts, te) == 12 + 6
+    assert bench.union_rows(np.array([7]), np.array([7])) == 1
+
+
+def test_union_rows_matches_brute_force():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        ts = rng.integers(0, 500, size=30)
+        te = ts + rng.integers(0, 60, size=30)
+        covered = np.zeros(600, dtype=bool)
+        for a, z in zip(ts, te):
+            covered[a:z + 1] = True
+        assert bench.union_rows(ts, te) == int(covered.sum())
+
+
+def test_lift_model_counts_writes_and_distinct_reads():
+    import synthetic
+    w = synthetic.WORKLOADS["compress_f32"]
+    bound, units = bench.kernel_model("lift", w, 1, 1000, 400)
+    assert bound == "hbm" and units == (1000 + 400) * w.k * 4
