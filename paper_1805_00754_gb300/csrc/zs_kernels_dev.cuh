@@ -140,6 +140,38 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
                           typename Prec<T, REF>::TR* theta, int* perm, typename Prec<T, REF>::TR*& Zo) {
     using TR = typename Prec<T, REF>::TR;
     const int tid = threadIdx.x, nt = blockDim.x, ld = s.ld;
+    if constexpr (std::is_same<T, float>::value && !REF) {
+        if (m <= 32) {
+            // one warp, in registers: Cholesky A = G G^T, then one-sided
+            // Jacobi on G's columns gives the eigenpairs (written sorted)
+            __shared__ float tile[32 * 33];
+            __syncthreads();
+            if (tid < 32) {
+                const int lane = tid;
+                float x[32], v[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) x[i] = (i < m && lane < m) ? s.A_T[i * ld + lane] : 0.f;
+                warp_chol32(x, tile, lane);
+                const float th = warp_hestenes32(x, v, lane);
+                int rk = 0;
+#pragma unroll
+                for (int o = 0; o < 32; ++o) {
+                    const float ot = __shfl_sync(0xffffffffu, th, o);
+                    rk += (ot > th) || (ot == th && o < lane);
+                }
+                if (rk < m) {
+                    theta[rk] = th;
+                    perm[rk] = rk;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < m) s.Z_T[i * ld + rk] = x[i];
+                }
+            }
+            __syncthreads();
+            Zo = reinterpret_cast<TR*>(s.Z_T);
+            return;
+        }
+    }
     const int sweeps = std::is_same<T, double>::value ? 40 : 30;
     jacobi_eig<T>(s.A_T, ld, s.Z_T, ld, m, js, sweeps, true);
     if constexpr (REF) {

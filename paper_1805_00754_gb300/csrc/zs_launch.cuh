@@ -158,12 +158,24 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
 
 template <typename T, int KMAX, int QMAX>
 static void lift_launch(const QueryArgs& a, int64_t max_slabs, int num_sms, cudaStream_t st) {
-    const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
-    const int wpc = threads / 32;
-    const size_t sm = sizeof(T) * (size_t)KMAX * QMAX * wpc;
-    set_smem(k_lift<T, KMAX, QMAX>, sm);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
-    k_lift<T, KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+    if constexpr (std::is_same<T, float>::value) {
+        // tensor-core lift: per warp two split copies of C in shared memory
+        const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;
+        const int wpc = threads / 32;
+        const size_t sm = sizeof(float) * lift_tc_warp_floats<KMAX, QMAX>() * wpc;
+        set_smem(k_lift_tc<KMAX, QMAX>, sm);
+        const int grid =
+            (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
+        k_lift_tc<KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+    } else {
+        const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
+        const int wpc = threads / 32;
+        const size_t sm = sizeof(T) * (size_t)KMAX * QMAX * wpc;
+        set_smem(k_lift<T, KMAX, QMAX>, sm);
+        const int grid =
+            (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
+        k_lift<T, KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+    }
 }
 
 template <typename T, int KMAX>

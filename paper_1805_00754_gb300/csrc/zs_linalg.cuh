@@ -334,4 +334,151 @@ __device__ void warp_sort_desc(const T* A, int lda, int m, int* perm) {
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident warp routines for one 32 x 32 problem per warp: lane l
+// holds column l.  Pairing is the round-robin schedule of rr_pair (index 0
+// fixed, 1..31 rotating) in closed form, so each lane finds its partner
+// without a table.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int rr_partner32(int x, int r) {
+    if (x == 0) return (r + 30) % 31 + 1;
+    int v = (2 * r - 2 - (x - 1)) % 31;
+    if (v < 0) v += 31;
+    const int y = v + 1;
+    return y == x ? 0 : y;
+}
+
+// The loops below run over the pivot index without unrolling (the code stays
+// small); the lane's vector is shifted down one register per step so that
+// the pivot element is always register 0 and every index stays static.
+
+// Cholesky A = L L^T of the warp's symmetric 32 x 32 matrix held as column
+// `lane` in a[].  L goes to the per-warp tile T (row-major, stride 33); on
+// return a[] holds column `lane` of L.  A pivot <= 0 gives a zero column.
+__device__ __forceinline__ void warp_chol32(float (&a)[32], float* T, int lane) {
+    for (int j = 0; j < 32; ++j) {
+        // a[0..31-j] hold rows j.. of column `lane`
+        const float piv = __shfl_sync(0xffffffffu, a[0], j);
+        const float d = piv > 0.f ? sqrtf(piv) : 0.f;
+        const float inv = d > 0.f ? 1.f / d : 0.f;
+        const float slj = a[0] * inv;                       // L[lane][j] for lane > j
+        if (lane == j) T[j * 33 + j] = d;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) {
+            const float lij = __shfl_sync(0xffffffffu, a[i], j) * inv;   // L[j+i][j]
+            if (lane == j && j + i < 32) T[(j + i) * 33 + j] = lij;
+            if (lane > j) a[i] = fmaf(-lij, slj, a[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 31; ++i) a[i] = a[i + 1];
+        a[31] = 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) a[i] = i >= lane ? T[i * 33 + lane] : 0.f;
+    __syncwarp();
+}
+
+// x = L^-1 h for every lane's own vector h (L row-major in T, stride 33).
+// The solution is also left in W as W[i][lane] (row-major, stride 33).
+__device__ __forceinline__ void warp_fsub32(const float* T, float (&h)[32], float (&x)[32], float* W, int lane) {
+    for (int p = 0; p < 32; ++p) {
+        const float dpp = T[p * 33 + p];
+        const float xp = dpp > 0.f ? h[0] / dpp : 0.f;
+        W[p * 33 + lane] = xp;
+#pragma unroll
+        for (int i = 1; i < 32; ++i)
+            if (p + i < 32) h[i] = fmaf(-T[(p + i) * 33 + p], xp, h[i]);
+#pragma unroll
+        for (int i = 0; i < 31; ++i) h[i] = h[i + 1];
+        h[31] = 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = W[i * 33 + lane];
+}
+
+// z = L^-T w for every lane's own vector w (L row-major in T); W as above.
+__device__ __forceinline__ void warp_bsub32(const float* T, float (&w)[32], float (&z)[32], float* W, int lane) {
+    for (int i = 31; i >= 0; --i) {
+        // w[31 - q] holds w_{i - q}
+        const float dii = T[i * 33 + i];
+        const float zi = dii > 0.f ? w[31] / dii : 0.f;
+        W[i * 33 + lane] = zi;
+#pragma unroll
+        for (int q = 1; q < 32; ++q)
+            if (q <= i) w[31 - q] = fmaf(-T[i * 33 + (i - q)], zi, w[31 - q]);
+#pragma unroll
+        for (int q = 31; q > 0; --q) w[q] = w[q - 1];
+        w[0] = 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) z[i] = W[i * 33 + lane];
+}
+
+// One-sided (Hestenes) Jacobi on the warp's 32 x 32 matrix G (column `lane`
+// in x[]; v[] is scratch): orthogonalises the columns of G by plane
+// rotations over the round-robin pairing.  On return x[] holds the unit
+// vector of column `lane` and the result is its squared norm: for G = R^T
+// with R^T R = A these are the eigenvectors and eigenvalues of A.
+__device__ __forceinline__ float warp_hestenes32(float (&x)[32], float (&v)[32], int lane) {
+    // one-sided Jacobi on the columns of G
+    float al = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+    // converged when every pair is orthogonal to 1e-5: safely above the
+    // rounding level of a 32-term fp32 dot product, which a tighter test
+    // could keep rotating at
+    const float tol = 1e-5f;
+    for (int sweep = 0; sweep < 15; ++sweep) {
+        int rotated = 0;
+        for (int r = 0; r < 31; ++r) {
+            const int pr = rr_partner32(lane, r);
+            const bool isp = lane < pr;
+            float g4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                v[i] = __shfl_sync(0xffffffffu, x[i], pr);
+                g4[i & 3] = fmaf(x[i], v[i], g4[i & 3]);
+            }
+            const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
+            const float ao = __shfl_sync(0xffffffffu, al, pr);
+            const float app = isp ? al : ao, aqq = isp ? ao : al;
+            float c = 1.f, s = 0.f;
+            if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
+                // zeta and t need only be near the optimum (the sweep
+                // repeats); c gets a Newton step so that c^2 + s^2 = 1 to
+                // rounding and the column norms do not drift
+                const float zeta = __fdividef(aqq - app, 2.f * g);
+                const float r1 = fmaf(zeta, zeta, 1.f);
+                const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + r1 * rsqrtf(r1));
+                const float u = fmaf(t, t, 1.f);
+                float cc = rsqrtf(u);
+                cc = cc * fmaf(-0.5f * u * cc, cc, 1.5f);
+                c = cc;
+                s = cc * t;
+                al = isp ? app - t * g : aqq + t * g;
+                rotated = 1;
+            }
+            // p: c x_p - s x_q; q: s x_p + c x_q (branch-free across the pair)
+            const float sv = isp ? -s : s;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = fmaf(sv, v[i], c * x[i]);
+        }
+        if (!__any_sync(0xffffffffu, rotated)) break;
+        al = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+    }
+    al = 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
+    const float sg = sqrtf(al);
+    const float inv = sg > 0.f ? 1.f / sg : 0.f;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] *= inv;
+    return al;
+}
+
 }  // namespace zs

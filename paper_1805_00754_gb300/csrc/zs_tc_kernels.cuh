@@ -1061,83 +1061,6 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
 //      schedule of zs_linalg.cuh (index 0 fixed, 1..31 rotating), in closed
 //      form so that each lane finds its partner without a table.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int rr_partner32(int x, int r) {
-    if (x == 0) return (r + 30) % 31 + 1;
-    int v = (2 * r - 2 - (x - 1)) % 31;
-    if (v < 0) v += 31;
-    const int y = v + 1;
-    return y == x ? 0 : y;
-}
-
-// The loops below run over the pivot index without unrolling (the code stays
-// small); the lane's vector is shifted down one register per step so that
-// the pivot element is always register 0 and every index stays static.
-
-// Cholesky A = L L^T of the warp's symmetric 32 x 32 matrix held as column
-// `lane` in a[].  L goes to the per-warp tile T (row-major, stride 33); on
-// return a[] holds column `lane` of L.  A pivot <= 0 gives a zero column.
-__device__ __forceinline__ void warp_chol32(float (&a)[32], float* T, int lane) {
-    for (int j = 0; j < 32; ++j) {
-        // a[0..31-j] hold rows j.. of column `lane`
-        const float piv = __shfl_sync(0xffffffffu, a[0], j);
-        const float d = piv > 0.f ? sqrtf(piv) : 0.f;
-        const float inv = d > 0.f ? 1.f / d : 0.f;
-        const float slj = a[0] * inv;                       // L[lane][j] for lane > j
-        if (lane == j) T[j * 33 + j] = d;
-#pragma unroll
-        for (int i = 1; i < 32; ++i) {
-            const float lij = __shfl_sync(0xffffffffu, a[i], j) * inv;   // L[j+i][j]
-            if (lane == j && j + i < 32) T[(j + i) * 33 + j] = lij;
-            if (lane > j) a[i] = fmaf(-lij, slj, a[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 31; ++i) a[i] = a[i + 1];
-        a[31] = 0.f;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = i >= lane ? T[i * 33 + lane] : 0.f;
-    __syncwarp();
-}
-
-// x = L^-1 h for every lane's own vector h (L row-major in T, stride 33).
-// The solution is also left in W as W[i][lane] (row-major, stride 33).
-__device__ __forceinline__ void warp_fsub32(const float* T, float (&h)[32], float (&x)[32], float* W, int lane) {
-    for (int p = 0; p < 32; ++p) {
-        const float dpp = T[p * 33 + p];
-        const float xp = dpp > 0.f ? h[0] / dpp : 0.f;
-        W[p * 33 + lane] = xp;
-#pragma unroll
-        for (int i = 1; i < 32; ++i)
-            if (p + i < 32) h[i] = fmaf(-T[(p + i) * 33 + p], xp, h[i]);
-#pragma unroll
-        for (int i = 0; i < 31; ++i) h[i] = h[i + 1];
-        h[31] = 0.f;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 32; ++i) x[i] = W[i * 33 + lane];
-}
-
-// z = L^-T w for every lane's own vector w (L row-major in T); W as above.
-__device__ __forceinline__ void warp_bsub32(const float* T, float (&w)[32], float (&z)[32], float* W, int lane) {
-    for (int i = 31; i >= 0; --i) {
-        // w[31 - q] holds w_{i - q}
-        const float dii = T[i * 33 + i];
-        const float zi = dii > 0.f ? w[31] / dii : 0.f;
-        W[i * 33 + lane] = zi;
-#pragma unroll
-        for (int q = 1; q < 32; ++q)
-            if (q <= i) w[31 - q] = fmaf(-T[i * 33 + (i - q)], zi, w[31 - q]);
-#pragma unroll
-        for (int q = 31; q > 0; --q) w[q] = w[q - 1];
-        w[0] = 0.f;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 32; ++i) z[i] = W[i * 33 + lane];
-}
-
 template <class Src>
 __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int kw) {
     __shared__ float tl[4][32 * 33];                  // per warp: Cholesky factor of C
@@ -1176,61 +1099,7 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
         warp_fsub32(TL, v, x, TW, lane);               // H' = L^-1 X^T, column `lane`
         __syncwarp();
         warp_chol32(x, TW, lane);                      // H' = G G^T, column `lane` of G
-        // one-sided Jacobi on the columns of G
-        float al = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
-        // converged when every pair is orthogonal to 1e-5: safely above the
-        // rounding level of a 32-term fp32 dot product, which a tighter test
-        // could keep rotating at
-        const float tol = 1e-5f;
-        for (int sweep = 0; sweep < 15; ++sweep) {
-            int rotated = 0;
-            for (int r = 0; r < 31; ++r) {
-                const int pr = rr_partner32(lane, r);
-                const bool isp = lane < pr;
-                float g4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    v[i] = __shfl_sync(0xffffffffu, x[i], pr);
-                    g4[i & 3] = fmaf(x[i], v[i], g4[i & 3]);
-                }
-                const float g = (g4[0] + g4[1]) + (g4[2] + g4[3]);
-                const float ao = __shfl_sync(0xffffffffu, al, pr);
-                const float app = isp ? al : ao, aqq = isp ? ao : al;
-                float c = 1.f, s = 0.f;
-                if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
-                    // zeta and t need only be near the optimum (the sweep
-                    // repeats); c gets a Newton step so that c^2 + s^2 = 1 to
-                    // rounding and the column norms do not drift
-                    const float zeta = __fdividef(aqq - app, 2.f * g);
-                    const float r1 = fmaf(zeta, zeta, 1.f);
-                    const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + r1 * rsqrtf(r1));
-                    const float u = fmaf(t, t, 1.f);
-                    float cc = rsqrtf(u);
-                    cc = cc * fmaf(-0.5f * u * cc, cc, 1.5f);
-                    c = cc;
-                    s = cc * t;
-                    al = isp ? app - t * g : aqq + t * g;
-                    rotated = 1;
-                }
-                // p: c x_p - s x_q; q: s x_p + c x_q (branch-free across the pair)
-                const float sv = isp ? -s : s;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) x[i] = fmaf(sv, v[i], c * x[i]);
-            }
-            if (!__any_sync(0xffffffffu, rotated)) break;
-            al = 0.f;
-#pragma unroll
-            for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
-        }
-        al = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) al = fmaf(x[i], x[i], al);
-        const float sg = sqrtf(al);
-        const float inv = sg > 0.f ? 1.f / sg : 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] *= inv;      // w = unit eigenvector of H'
+        const float al = warp_hestenes32(x, v, lane);
         // rank of this lane's theta (descending, lower lane first on ties)
         int rk = 0;
 #pragma unroll
@@ -1421,6 +1290,104 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
                     } else {
                         up[0] = acc[q][2 * h];
                         if (c + 1 < kw) up[1] = acc[q][2 * h + 1];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 5. Lift on tf32 tensor cores (float stores): the rows of U_{S:E} are the
+//    stored U_i rows times each slab's coefficients C (k x kq) (Algorithm 2,
+//    last step; Eq. 9), one warp per slab, 16 rows per step.  U rows and C are
+//    split into two tf32 terms each (three products: FP32-grade results); C is
+//    split once per slab into two shared tiles.
+// ---------------------------------------------------------------------------
+template <int QMAX>
+__host__ __device__ constexpr int lift_ldc() { return (QMAX + 31) / 32 * 32 + 8; }
+template <int KMAX, int QMAX>
+__host__ __device__ __forceinline__ size_t lift_tc_warp_floats() { return (size_t)2 * KMAX * lift_ldc<QMAX>(); }
+
+template <int KMAX, int QMAX>
+__global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
+    extern __shared__ __align__(16) float lsm[];
+    constexpr int LDC = lift_ldc<QMAX>();
+    const int k = a.k, kq = a.kq, kout = a.kout;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    float* Ch = lsm + (size_t)warp * lift_tc_warp_floats<KMAX, QMAX>();
+    float* Cl = Ch + KMAX * LDC;
+    const int nq = a.hdr->nq;
+    const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
+    const int nkt = (k + 7) / 8, nnt = (kout + 7) / 8;
+    for (int64_t s = (int64_t)blockIdx.x * wpc + warp; s < total; s += (int64_t)gridDim.x * wpc) {
+        const int q = find_query(a.slab_prefix, nq, s);
+        const QPlan& P = a.plans[q];
+        const int t = (int)(s - P.slab0);
+        const BlockRange br = slab_rows(P, t, a.b, Trows);
+        const float* U = (const float*)a.U + (int64_t)br.blk * a.b * k;
+        const float* Cg = (const float*)a.C + s * k * kq;
+        __syncwarp();
+        for (int e = lane; e < KMAX * QMAX; e += 32) {
+            const int aa = e / QMAX, c = e % QMAX;
+            const float v = (aa < k && c < kq) ? Cg[aa * kq + c] : 0.f;
+            uint32_t h, l;
+            tf32_split(v, h, l);
+            Ch[aa * LDC + c] = __uint_as_float(h);
+            Cl[aa * LDC + c] = __uint_as_float(l);
+        }
+        __syncwarp();
+        float* out = (float*)P.U;
+        const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
+        const bool pair = (kout % 2 == 0) && (P.ldu % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+        for (int r0 = br.lo; r0 < br.hi; r0 += 16) {
+            float acc[QMAX / 8][4];
+#pragma unroll
+            for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+            const int ra = r0 + g, rb = r0 + g + 8;
+            const bool va = ra < br.hi, vb = rb < br.hi;
+            const float* pa = U + (int64_t)ra * k;
+            const float* pb = U + (int64_t)rb * k;
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt) {
+                if (kt >= nkt) break;
+                const int c0 = kt * 8 + t4, c1 = c0 + 4;
+                const float x0 = (va && c0 < k) ? __ldg(pa + c0) : 0.f;
+                const float x1 = (vb && c0 < k) ? __ldg(pb + c0) : 0.f;
+                const float x2 = (va && c1 < k) ? __ldg(pa + c1) : 0.f;
+                const float x3 = (vb && c1 < k) ? __ldg(pb + c1) : 0.f;
+                uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+                tf32_split_trunc(x0, h0, l0);
+                tf32_split_trunc(x1, h1, l1);
+                tf32_split_trunc(x2, h2, l2);
+                tf32_split_trunc(x3, h3, l3);
+                const float* bh = Ch + c0 * LDC + g;
+                const float* bl = Cl + c0 * LDC + g;
+#pragma unroll
+                for (int nt = 0; nt < QMAX / 8; ++nt) {
+                    if (nt >= nnt) break;
+                    const uint32_t bh0 = __float_as_uint(bh[nt * 8]), bh1 = __float_as_uint(bh[4 * LDC + nt * 8]);
+                    const uint32_t bl0 = __float_as_uint(bl[nt * 8]), bl1 = __float_as_uint(bl[4 * LDC + nt * 8]);
+                    mma_tf32(acc[nt], l0, l1, l2, l3, bh0, bh1);
+                    mma_tf32(acc[nt], h0, h1, h2, h3, bl0, bl1);
+                    mma_tf32(acc[nt], h0, h1, h2, h3, bh0, bh1);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < QMAX / 8; ++nt) {
+                if (nt >= nnt) break;
+                const int c = nt * 8 + 2 * t4;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int r = hh ? rb : ra;
+                    if (r >= br.hi || c >= kout) continue;
+                    float* orow = out + (o0 + r) * P.ldu + c;
+                    if (pair) {
+                        *reinterpret_cast<float2*>(orow) = make_float2(acc[nt][2 * hh], acc[nt][2 * hh + 1]);
+                    } else {
+                        orow[0] = acc[nt][2 * hh];
+                        if (c + 1 < kout) orow[1] = acc[nt][2 * hh + 1];
                     }
                 }
             }
