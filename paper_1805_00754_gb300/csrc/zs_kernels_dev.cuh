@@ -700,12 +700,24 @@ __global__ void __launch_bounds__(256) k_stack(QueryArgs a) {
                 const int n4 = n >> 2;
                 const float4* v4 = reinterpret_cast<const float4*>(vt);
                 float4* m4 = reinterpret_cast<float4*>(Ms);
-                for (int e = threadIdx.x; e < k * n4; e += blockDim.x) {
-                    const int j = e / n4;
-                    const float sj = __ldg(sg + j);
-                    float4 v = __ldg(v4 + e);
-                    v.x *= sj; v.y *= sj; v.z *= sj; v.w *= sj;
-                    m4[e] = v;
+                const int tot = k * n4, stride = blockDim.x;
+                // four loads in flight per thread before the stores
+                for (int e0 = threadIdx.x; e0 < tot; e0 += 4 * stride) {
+                    float4 v[4];
+                    float sj[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * stride;
+                        if (e < tot) {
+                            v[u] = __ldg(v4 + e);
+                            sj[u] = __ldg(sg + e / n4);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int e = e0 + u * stride;
+                        if (e < tot) m4[e] = make_float4(v[u].x * sj[u], v[u].y * sj[u], v[u].z * sj[u], v[u].w * sj[u]);
+                    }
                 }
                 continue;
             }

@@ -210,9 +210,15 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         auto r16 = [](size_t b) { return (b + 15) & ~size_t(15); };
         size_t sm = 2 * r16(sizeof(T) * k * ld) + r16(sizeof(T) * 64 * ld);
         if (REF) sm += 3 * r16(sizeof(double) * k * ld);
-        ZS_TRY(set_smem(k_partial<T, REF>, sm));
         prof::Scope ps("partial_svd", st);
-        k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+        if (std::is_same<T, float>::value && !REF && k <= 32) {
+            // one warp per boundary slab (2 per query), 4 warps per CTA
+            if (k <= 16) k_partial_warp<16><<<(2 * max_nq + 3) / 4, 128, 0, st>>>(a);
+            else k_partial_warp<32><<<(2 * max_nq + 3) / 4, 128, 0, st>>>(a);
+        } else {
+            ZS_TRY(set_smem(k_partial<T, REF>, sm));
+            k_partial<T, REF><<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
+        }
         ZS_TRY(cudaGetLastError());
     }
     {

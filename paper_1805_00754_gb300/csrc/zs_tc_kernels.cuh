@@ -1341,27 +1341,44 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
         float* out = (float*)P.U;
         const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
         const bool pair = (kout % 2 == 0) && (P.ldu % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
-        for (int r0 = br.lo; r0 < br.hi; r0 += 16) {
-            float acc[QMAX / 8][4];
-#pragma unroll
-            for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+        // U fragments of the next 16-row step are loaded before the current
+        // step's products (software pipeline over the slab's rows)
+        float nx[KMAX / 8][4];
+        auto fetch = [&](int r0, float (&dst)[KMAX / 8][4]) {
             const int ra = r0 + g, rb = r0 + g + 8;
             const bool va = ra < br.hi, vb = rb < br.hi;
             const float* pa = U + (int64_t)ra * k;
             const float* pb = U + (int64_t)rb * k;
 #pragma unroll
             for (int kt = 0; kt < KMAX / 8; ++kt) {
-                if (kt >= nkt) break;
                 const int c0 = kt * 8 + t4, c1 = c0 + 4;
-                const float x0 = (va && c0 < k) ? __ldg(pa + c0) : 0.f;
-                const float x1 = (vb && c0 < k) ? __ldg(pb + c0) : 0.f;
-                const float x2 = (va && c1 < k) ? __ldg(pa + c1) : 0.f;
-                const float x3 = (vb && c1 < k) ? __ldg(pb + c1) : 0.f;
+                dst[kt][0] = (kt < nkt && va && c0 < k) ? __ldg(pa + c0) : 0.f;
+                dst[kt][1] = (kt < nkt && vb && c0 < k) ? __ldg(pb + c0) : 0.f;
+                dst[kt][2] = (kt < nkt && va && c1 < k) ? __ldg(pa + c1) : 0.f;
+                dst[kt][3] = (kt < nkt && vb && c1 < k) ? __ldg(pb + c1) : 0.f;
+            }
+        };
+        if (br.lo < br.hi) fetch(br.lo, nx);
+        for (int r0 = br.lo; r0 < br.hi; r0 += 16) {
+            float cx[KMAX / 8][4];
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cx[kt][e] = nx[kt][e];
+            if (r0 + 16 < br.hi) fetch(r0 + 16, nx);
+            float acc[QMAX / 8][4];
+#pragma unroll
+            for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+            const int ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt) {
+                if (kt >= nkt) break;
+                const int c0 = kt * 8 + t4;
                 uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-                tf32_split_trunc(x0, h0, l0);
-                tf32_split_trunc(x1, h1, l1);
-                tf32_split_trunc(x2, h2, l2);
-                tf32_split_trunc(x3, h3, l3);
+                tf32_split_trunc(cx[kt][0], h0, l0);
+                tf32_split_trunc(cx[kt][1], h1, l1);
+                tf32_split_trunc(cx[kt][2], h2, l2);
+                tf32_split_trunc(cx[kt][3], h3, l3);
                 const float* bh = Ch + c0 * LDC + g;
                 const float* bl = Cl + c0 * LDC + g;
 #pragma unroll
@@ -1392,6 +1409,165 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
                 }
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Partial-SVD (Algorithm 3; Eq. 5-6) of one boundary slab per warp, float
+// stores with k <= KB <= 32:
+//   H = Sigma (X U)^T (X U) Sigma over the slab's rows on tf32 tensor cores
+//       (U split in two terms, three products; each row segment loaded once
+//       serves both operands),
+//   H = G G^T, one-sided Jacobi on G's columns -> V~, Sigma~^2 (sorted),
+//   slab rows Sigma~ V~^T V^T of M (another small tensor-core product) and
+//   the lift coefficient Sigma V~ Sigma~^{-1}.
+// ---------------------------------------------------------------------------
+template <int KB>
+__global__ void __launch_bounds__(128) k_partial_warp(QueryArgs a) {
+    constexpr int MT = KB / 16, NT = KB / 8, KT = KB / 8;
+    __shared__ float tiles[4][2][32 * 33];            // per warp: work tile, sorted V~
+    __shared__ float sts[4][32];                      // per warp: sorted Sigma~
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const int p = blockIdx.x * 4 + warp;
+    const int nq = a.hdr->nq;
+    if (p >= 2 * nq) return;
+    const int q = p >> 1, side = p & 1;
+    const QPlan& P = a.plans[q];
+    if (side == 1 && P.nslab == 1) return;
+    const int t = side ? P.nslab - 1 : 0;
+    const int k = a.k, n = a.n;
+    const BlockRange br = slab_rows(P, t, a.b, a.hdr->T);
+    const int ki = min(k, min(br.rows_i, n));
+    const float* U = (const float*)a.U + (int64_t)br.blk * a.b * k;
+    const float* sg = (const float*)a.sig + (int64_t)br.blk * k;
+    const float* vt = (const float*)a.vt + (int64_t)br.blk * k * n;
+    float* T = tiles[warp][0];
+    float* Zs = tiles[warp][1];
+    float* st = sts[warp];
+    // 1. Gram of the slab's rows of U
+    float h[MT][NT][4];
+#pragma unroll
+    for (int x = 0; x < MT; ++x)
+#pragma unroll
+        for (int y = 0; y < NT; ++y) h[x][y][0] = h[x][y][1] = h[x][y][2] = h[x][y][3] = 0.f;
+    float n0[NT], n1[NT];
+    auto fetch = [&](int r0) {
+        const int ra = r0 + t4, rb = r0 + t4 + 4;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            const int c = g + 8 * j;
+            n0[j] = (ra < br.hi && c < ki) ? __ldg(U + (int64_t)ra * k + c) : 0.f;
+            n1[j] = (rb < br.hi && c < ki) ? __ldg(U + (int64_t)rb * k + c) : 0.f;
+        }
+    };
+    if (br.lo < br.hi) fetch(br.lo);
+    for (int r0 = br.lo; r0 < br.hi; r0 += 8) {
+        uint32_t h0[NT], l0[NT], h1[NT], l1[NT];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            tf32_split(n0[j], h0[j], l0[j]);
+            tf32_split(n1[j], h1[j], l1[j]);
+        }
+        if (r0 + 8 < br.hi) fetch(r0 + 8);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+                mma_tf32(h[mt][nt], l0[2 * mt], l0[2 * mt + 1], l1[2 * mt], l1[2 * mt + 1], h0[nt], h1[nt]);
+                mma_tf32(h[mt][nt], h0[2 * mt], h0[2 * mt + 1], h1[2 * mt], h1[2 * mt + 1], l0[nt], l1[nt]);
+                mma_tf32(h[mt][nt], h0[2 * mt], h0[2 * mt + 1], h1[2 * mt], h1[2 * mt + 1], h0[nt], h1[nt]);
+            }
+    }
+    // H -> column `lane` in registers, scaled by sigma_i sigma_j
+    float sgl = lane < ki ? sg[lane] : 0.f;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int i = mt * 16 + g + ((e >> 1) ? 8 : 0), j = nt * 8 + 2 * t4 + (e & 1);
+                T[i * 33 + j] = h[mt][nt][e];
+            }
+    __syncwarp();
+    float x[32], v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const float si = __shfl_sync(0xffffffffu, sgl, i);
+        x[i] = (i < ki && lane < ki) ? T[i * 33 + lane] * si * sgl : 0.f;
+    }
+    __syncwarp();
+    // 2. eigenpairs of H
+    warp_chol32(x, T, lane);
+    const float th = warp_hestenes32(x, v, lane);
+    int rk = 0;
+#pragma unroll
+    for (int o = 0; o < 32; ++o) {
+        const float ot = __shfl_sync(0xffffffffu, th, o);
+        rk += (ot > th) || (ot == th && o < lane);
+    }
+    // keep r = min(rows, ki) pairs (the rank of X U Sigma), above the rank tolerance
+    const int r = min(br.hi - br.lo, ki);
+    float sv = rk < r ? sqrtf(fmaxf(th, 0.f)) : 0.f;
+    float s0 = sv;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s0 = fmaxf(s0, __shfl_xor_sync(0xffffffffu, s0, o));
+    if (!(sv > kRankTolF32 * s0)) sv = 0.f;
+    st[rk] = sv;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Zs[i * 33 + rk] = x[i];
+    __syncwarp();
+    // 3. lift coefficient Sigma V~ Sigma~^{-1} (k x k)
+    float* tc = (float*)a.tco + (int64_t)p * k * k;
+    for (int e = lane; e < k * k; e += 32) {
+        const int aa = e / k, j = e - (e / k) * k;
+        const float sj = st[j];
+        tc[e] = (aa < ki && sj > 0.f) ? sg[aa] * Zs[aa * 33 + j] / sj : 0.f;
+    }
+    // 4. slab rows of M: Ms[j][l] = Sigma~_j sum_aa V~[aa][j] Vt[aa][l]
+    uint32_t ah[KT][MT][4], al[KT][MT][4];
+#pragma unroll
+    for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const int r0 = kt * 8 + t4, jr = mt * 16 + g;
+            tf32_split(Zs[r0 * 33 + jr], ah[kt][mt][0], al[kt][mt][0]);
+            tf32_split(Zs[r0 * 33 + jr + 8], ah[kt][mt][1], al[kt][mt][1]);
+            tf32_split(Zs[(r0 + 4) * 33 + jr], ah[kt][mt][2], al[kt][mt][2]);
+            tf32_split(Zs[(r0 + 4) * 33 + jr + 8], ah[kt][mt][3], al[kt][mt][3]);
+        }
+    float* Ms = (float*)a.M + (P.slab0 + t) * k * n;
+    for (int l0 = 0; l0 < n; l0 += 8) {
+        float c[MT][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) c[mt][0] = c[mt][1] = c[mt][2] = c[mt][3] = 0.f;
+        const int l = l0 + g;
+#pragma unroll
+        for (int kt = 0; kt < KT; ++kt) {
+            const int r0 = kt * 8 + t4;
+            const float b0 = (r0 < ki && l < n) ? __ldg(vt + (int64_t)r0 * n + l) : 0.f;
+            const float b1 = (r0 + 4 < ki && l < n) ? __ldg(vt + (int64_t)(r0 + 4) * n + l) : 0.f;
+            uint32_t bh0, bl0, bh1, bl1;
+            tf32_split(b0, bh0, bl0);
+            tf32_split(b1, bh1, bl1);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                mma_tf32(c[mt], al[kt][mt][0], al[kt][mt][1], al[kt][mt][2], al[kt][mt][3], bh0, bh1);
+                mma_tf32(c[mt], ah[kt][mt][0], ah[kt][mt][1], ah[kt][mt][2], ah[kt][mt][3], bl0, bl1);
+                mma_tf32(c[mt], ah[kt][mt][0], ah[kt][mt][1], ah[kt][mt][2], ah[kt][mt][3], bh0, bh1);
+            }
+        }
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = mt * 16 + g + ((e >> 1) ? 8 : 0), ll = l0 + 2 * t4 + (e & 1);
+                if (j < k && ll < n) {
+                    const float sj = st[j];
+                    Ms[(int64_t)j * n + ll] = sj > 0.f ? sj * c[mt][e] : 0.f;
+                }
+            }
     }
 }
 
