@@ -226,6 +226,7 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.U = st.U;
     a.sig = st.sig;
     a.vt = st.vt;
+    a.wst = st.w;
     a.b = (int32_t)st.cfg.b;
     a.n = (int32_t)st.cfg.n;
     a.k = st.cfg.k;
@@ -307,6 +308,8 @@ static zs_status store_alloc(zs_store* st) {
     if ((s = al(&st->U, ts * nb * c.b * c.k, "store U")) != ZS_OK) return s;
     if ((s = al(&st->sig, ts * nb * c.k, "store sigma")) != ZS_OK) return s;
     if ((s = al(&st->vt, ts * nb * c.k * c.n, "store V")) != ZS_OK) return s;
+    if (use_tc_path(st->fp64, (int)c.n, c.flags))
+        if ((s = al(&st->w, ts * nb * c.k * c.n, "store Sigma V^T")) != ZS_OK) return s;
     if ((s = al(&st->tail, st->insize * (size_t)c.b * c.n, "open-block rows")) != ZS_OK) return s;
     // Gram scratch: chunk of blocks whose n x n Grams stay L2-sized
     const size_t gper = ts * (size_t)c.n * c.n;
@@ -353,6 +356,7 @@ static zs_status store_alloc(zs_store* st) {
     ZS_CU(cudaMemset(st->U, 0, ts * nb * c.b * c.k), "memset");
     ZS_CU(cudaMemset(st->sig, 0, ts * nb * c.k), "memset");
     ZS_CU(cudaMemset(st->vt, 0, ts * nb * c.k * c.n), "memset");
+    if (st->w) ZS_CU(cudaMemset(st->w, 0, ts * nb * c.k * c.n), "memset");
     ZS_CU(cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking), "stream");
     // chunk pipeline (tensor path with the sketch kernel: no shared per-CTA workspace)
     if (use_tc_path(st->fp64, (int)c.n, c.flags) &&
@@ -429,7 +433,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     cudaDeviceSynchronize();
     st->qx.release();
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
-    f(st->U); f(st->sig); f(st->vt); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
+    f(st->U); f(st->sig); f(st->vt); f(st->w); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
     f(st->qb); f(st->ys); f(st->aux);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
@@ -487,6 +491,7 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
             ch.U = st->U;
             ch.sig = st->sig;
             ch.vt = st->vt;
+            ch.w = st->w;
             ch.ews = st->ews;
             ch.ews_ctas = st->ews_ctas;
             ch.qb = (char*)st->qb + (size_t)r * sub * 4 * m * c.n;
@@ -519,6 +524,7 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.U = st->U;
         ch.sig = st->sig;
         ch.vt = st->vt;
+        ch.w = st->w;
         ch.ews = st->ews;
         ch.ews_ctas = st->ews_ctas;
         ch.qb = st->qb;

@@ -63,6 +63,7 @@ struct zs_store {
     void* U = nullptr;             // cap_blocks x b x k
     void* sig = nullptr;           // cap_blocks x k
     void* vt = nullptr;            // cap_blocks x k x n
+    void* w = nullptr;             // tensor path: cap_blocks x k x n, Sigma V^T (the stack-ready slabs)
     void* tail = nullptr;          // b x n raw rows of the open block
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace

@@ -34,6 +34,7 @@ struct CompressChunk {
     void* U;          // store: slot-major, b * k per slot
     void* sig;        // store: k per slot
     void* vt;         // store: k * n per slot
+    void* w;          // store (tensor path, optional): Sigma V^T, k * n per slot
     void* ews;        // eigen-core workspace (ews_ctas CTAs x n x 65 elements)
     int32_t ews_ctas;
     void* qb;         // tensor path: nblk x n x m subspace bases (fp32 holding tf32 values)
@@ -88,6 +89,7 @@ struct QueryArgs {
     const void* U;
     const void* sig;
     const void* vt;
+    const void* wst;  // tensor path: store Sigma V^T (interior slabs read from it), or null
     int32_t b, n, k;
     int32_t kq;                   // eigenpairs computed per query (= min(k_out, n))
     int32_t kout;

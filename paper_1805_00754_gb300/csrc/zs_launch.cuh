@@ -221,11 +221,12 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         }
         ZS_TRY(cudaGetLastError());
     }
-    {
+    if (!(tc && a.wst)) {      // interior slabs are read in place from the store's Sigma V^T otherwise
         prof::Scope ps("stack", st);
         k_stack<T><<<(int)std::min<int64_t>(max_slabs, pers), 256, 0, st>>>(a);
+        ZS_TRY(cudaGetLastError());
+        note_launches(1);
     }
-    ZS_TRY(cudaGetLastError());
     if constexpr (!std::is_same<T, double>::value) {
         if (tc) {
             TcScratch sc;
@@ -250,7 +251,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             {
                 ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
             }
-            note_launches(4);
+            note_launches(3);
             return cudaSuccess;
         }
     }
@@ -285,7 +286,7 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         ZS_TRY(cudaGetLastError());
     }
     ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
-    note_launches(6);
+    note_launches(5);
     return cudaSuccess;
 }
 

@@ -76,15 +76,26 @@ struct SrcQuery {
         return (const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem;
     }
     __device__ __forceinline__ int64_t ybase(int q) const { return a.plans[q].slab0 * a.k; }
-    // row r of query q's stacked matrix M (Algorithm 2, stack step; written by
-    // the Partial-SVD and stack kernels)
-    struct Ctx { const char* base; };
+    // row r of query q's stacked matrix M (Algorithm 2, stack step).  The two
+    // boundary slabs are written to M by the Partial-SVD kernel; the interior
+    // slabs are the store's Sigma_i V_i^T, read in place when the store keeps
+    // them (wst) and otherwise copied into M by the stack kernel.
+    // kmagic = ceil(2^32 / k): the slab of row r is umulhi(r, kmagic), exact
+    // for r < 2^32 / k (no integer division per row)
+    struct Ctx { const char* base; const char* wbase; int nslab; uint32_t kmagic; };
     __device__ __forceinline__ Ctx ctx(int q, int elem) const {
-        return Ctx{(const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem};
+        const QPlan& P = a.plans[q];
+        return Ctx{(const char*)a.M + (size_t)P.slab0 * a.k * a.n * elem,
+                   a.wst ? (const char*)a.wst + (size_t)P.S * a.k * a.n * elem : nullptr, P.nslab,
+                   (uint32_t)((0x100000000ull + (uint64_t)a.k - 1) / (uint64_t)a.k)};
     }
     template <typename Tin>
     __device__ __forceinline__ const Tin* row(const Ctx& x, int r, float& scale) const {
         scale = 1.f;
+        if (x.wbase) {
+            const int t = (int)__umulhi((uint32_t)r, x.kmagic);
+            if (t > 0 && t < x.nslab - 1) return (const Tin*)x.wbase + (size_t)r * a.n;
+        }
         return (const Tin*)x.base + (size_t)r * a.n;
     }
     __device__ __forceinline__ int64_t tile0(int q) const { return a.plans[q].pad0; }
@@ -386,6 +397,7 @@ __global__ void __launch_bounds__(256, 3) k_project(Src src, TcScratch sc, int n
         const int r0 = rt * 128;
         if (r0 >= rows) continue;
         const char* X = (const char*)src.X(item, sizeof(Tin));
+        const auto cx = src.ctx(item, sizeof(Tin));
         const float* Qg = sc.Qf + (size_t)item * n * m;
         const bool async_x = kF32 && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
         const bool async_q = (m % 4 == 0) && ((reinterpret_cast<uintptr_t>(Qg) & 15) == 0);
@@ -398,16 +410,17 @@ __global__ void __launch_bounds__(256, 3) k_project(Src src, TcScratch sc, int n
                 const int r = f / (kPjKC / 4), c4 = (f - r * (kPjKC / 4)) * 4;
                 const int gr = r0 + r, gc = k0 + c4;
                 float* dst = Xs + r * kPjLDX + c4;
+                float rs;
                 if (async_x) {
                     const int nb = (gr < rows && gc < n) ? 4 * min(4, n - gc) : 0;
-                    const float* sp = nb ? (const float*)X + (size_t)gr * ld + gc : (const float*)X;
+                    const float* sp = nb ? (const float*)src.template row<Tin>(cx, gr, rs) + gc : (const float*)X;
                     cp_async16(dst, sp, nb);
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         float v = 0.f;
                         if (gr < rows && gc + e < n) {
-                            const Tin* p = (const Tin*)X + (size_t)gr * ld + gc + e;
+                            const Tin* p = src.template row<Tin>(cx, gr, rs) + gc + e;
                             if constexpr (kF32) v = __ldg(p);
                             else v = __bfloat162float(*p);
                         }
@@ -1260,9 +1273,15 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
             float* so = (float*)src.c.sig + (size_t)slot * src.c.k;
             for (int c = tid; c < src.c.k; c += nt) so[c] = c < kw ? sig[c] : 0.f;
         }
+        float* w_out = nullptr;
+        if constexpr (!QUERY) {
+            if (src.c.w) w_out = (float*)src.c.w + (size_t)(src.c.slot0 + item) * src.c.k * n;
+        }
         for (int e = tid; e < kw * n; e += nt) {
             const int c = e / n, l = e - (e / n) * n;
-            vt_out[e] = sig[c] > 0.f ? sgnf[c] * Vs[l * ldv + c] : 0.f;
+            const float vv = sig[c] > 0.f ? sgnf[c] * Vs[l * ldv + c] : 0.f;
+            vt_out[e] = vv;
+            if (w_out) w_out[e] = sig[c] * vv;      // Sigma V^T, the stack-ready slab
         }
         // fold sign / sigma into Z so that U = Y Zsm
         __syncthreads();
@@ -1321,8 +1340,14 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
     const int nq = a.hdr->nq;
     const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
     const int nkt = (k + 7) / 8, nnt = (kout + 7) / 8;
-    for (int64_t s = (int64_t)blockIdx.x * wpc + warp; s < total; s += (int64_t)gridDim.x * wpc) {
-        const int q = find_query(a.slab_prefix, nq, s);
+    // each warp takes a contiguous range of slabs, so the owning query only
+    // advances (one search per warp instead of one per slab)
+    const int64_t nw = (int64_t)gridDim.x * wpc, wid = (int64_t)blockIdx.x * wpc + warp;
+    const int64_t per = (total + nw - 1) / nw;
+    const int64_t s_lo = wid * per, s_hi = min(total, s_lo + per);
+    int q = s_lo < s_hi ? find_query(a.slab_prefix, nq, s_lo) : 0;
+    for (int64_t s = s_lo; s < s_hi; ++s) {
+        while (q + 1 < nq && a.slab_prefix[q + 1] <= s) ++q;
         const QPlan& P = a.plans[q];
         const int t = (int)(s - P.slab0);
         const BlockRange br = slab_rows(P, t, a.b, Trows);
