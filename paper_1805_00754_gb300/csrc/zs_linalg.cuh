@@ -446,7 +446,7 @@ __device__ __forceinline__ float warp_hestenes32(float (&x)[32], float (&v)[32],
             const float ao = __shfl_sync(0xffffffffu, al, pr);
             const float app = isp ? al : ao, aqq = isp ? ao : al;
             float c = 1.f, s = 0.f;
-            if (fabsf(g) > tol * sqrtf(app * aqq) && g != 0.f) {
+            if (g * g > (tol * tol) * (app * aqq) && g != 0.f) {
                 // zeta and t need only be near the optimum (the sweep
                 // repeats); c gets a Newton step so that c^2 + s^2 = 1 to
                 // rounding and the column norms do not drift

@@ -1093,16 +1093,23 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
         const float* Cq = sc.Cq + (size_t)item * m * m;
         float lc[32], v[32], x[32];
         // columns of H (sum of the tiles, fixed order) and of C, identity-padded
+        // unconditional loads from clamped addresses (then a select), so that
+        // each group of 32 loads is issued at once rather than one by one
+        const int lc_ = min(lane, m - 1);
+        const bool lok = lane < m;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
+            const float cv = __ldg(Cq + min(i, m - 1) * m + lc_);
             v[i] = 0.f;
-            lc[i] = (i < m && lane < m) ? Cq[i * m + lane] : (i == lane ? 1.f : 0.f);
+            lc[i] = (i < m && lok) ? cv : (i == lane ? 1.f : 0.f);
         }
         for (int t = 0; t < ntiles; ++t) {
             const float* hp = Hp + (size_t)t * m * m;
+            float hv[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-                if (i < m && lane < m) v[i] += hp[i * m + lane];
+            for (int i = 0; i < 32; ++i) hv[i] = __ldg(hp + min(i, m - 1) * m + lc_);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += (i < m && lok) ? hv[i] : 0.f;
         }
         warp_chol32(lc, TL, lane);                     // C = L L^T, L in TL
         warp_fsub32(TL, v, x, TW, lane);               // X = L^-1 H, column `lane` (also in TW)
