@@ -255,8 +255,14 @@ def run_gpu(args, w):
     A = _input_rows(w)
     rows_dev = torch.from_numpy(A).to(f"cuda:{local}")
     in_bytes = T * n * itemsize
-    nq = args.nq if args.nq is not None else w.nq
-    ts, te = synthetic.queries(T, nq, w.lmin, w.lmax, seed=synthetic.SEED_BASE + 99)
+    if w.single_query is not None and args.nq is None:
+        # the plain workload's one query (t_s, t_e)
+        ts = np.array([w.single_query[0]], dtype=np.int64)
+        te = np.array([w.single_query[1]], dtype=np.int64)
+    else:
+        nq = args.nq if args.nq is not None else w.nq
+        ts, te = synthetic.queries(T, nq, w.lmin, w.lmax, seed=synthetic.SEED_BASE + 99)
+    nq = len(ts)
     st = zs.Store(n=n, b=b, k=k, dtype=w.dtype, capacity_rows=T, device=local,
                   fp64_refine=(w.dtype == "bf16"))
     outs = [st.new_result(int(a), int(z), k) for a, z in zip(ts, te)]

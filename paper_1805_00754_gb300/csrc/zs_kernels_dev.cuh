@@ -140,7 +140,8 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
                           typename Prec<T, REF>::TR* theta, int* perm, typename Prec<T, REF>::TR*& Zo) {
     using TR = typename Prec<T, REF>::TR;
     const int tid = threadIdx.x, nt = blockDim.x, ld = s.ld;
-    if constexpr (std::is_same<T, float>::value && !REF) {
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
         if (m <= 32) {
             // one warp, in registers: Cholesky A = G G^T, then one-sided
             // Jacobi on G's columns gives the eigenpairs (written sorted)
@@ -160,7 +161,7 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
                     rk += (ot > th) || (ot == th && o < lane);
                 }
                 if (rk < m) {
-                    theta[rk] = th;
+                    if (!REF) theta[rk] = th;
                     perm[rk] = rk;
 #pragma unroll
                     for (int i = 0; i < 32; ++i)
@@ -168,12 +169,15 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
                 }
             }
             __syncthreads();
-            Zo = reinterpret_cast<TR*>(s.Z_T);
-            return;
+            if constexpr (!REF) {
+                Zo = reinterpret_cast<TR*>(s.Z_T);
+                return;
+            }
+            done = true;
         }
     }
     const int sweeps = std::is_same<T, double>::value ? 40 : 30;
-    jacobi_eig<T>(s.A_T, ld, s.Z_T, ld, m, js, sweeps, true);
+    if (!done) jacobi_eig<T>(s.A_T, ld, s.Z_T, ld, m, js, sweeps, true);
     if constexpr (REF) {
         for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e - (e / m) * m;
@@ -189,7 +193,9 @@ __device__ void small_eig(SmallEig<T, REF>& s, int m, JacobiScratch<T>& js, Jaco
             s.A_R[a * ld + c] = acc;
         }
         __syncthreads();
-        jacobi_eig<double>(s.A_R, ld, s.W, ld, m, jd, 4, true);
+        // one FP64 refinement sweep (closed form: A_R is diagonal to FP32 rounding)
+        refine_sweep<double>(s.A_R, ld, s.W, ld, m, tid, nt, reinterpret_cast<double*>(theta),
+                             [] { __syncthreads(); });
         for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e - (e / m) * m;
             double acc = 0;

@@ -52,6 +52,9 @@ static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, 
 // The sketch kernel covers n <= 512 with its accumulator S (n x m) held in
 // registers: 16 NMT rows per warp, m <= MB.
 static inline bool sketch_fits(int n, int m) {
+    // n > 256 with m > 32 stays on the bf16-Gram route: its subspace (pivoted
+    // columns and a power step) is one power of X^T X ahead of the sketch's,
+    // which the precision workload's k = 32 of 40 signal directions needs
     if (n > 512 || (n > 256 && m > 32)) return false;
     return sketch_smem(n, m).total <= 227 * 1024 && (size_t)n * (m + 1) * 4 <= 227 * 1024;
 }

@@ -334,6 +334,38 @@ __device__ void warp_sort_desc(const T* A, int lda, int m, int* perm) {
     __syncwarp();
 }
 
+// One refinement sweep in closed form for a nearly diagonal symmetric B (the
+// FP64 Rayleigh quotient Z^T A Z of FP32 eigenvectors Z): the rotations of a
+// Jacobi sweep over such a B have angles B_ij / (B_jj - B_ii) to first order,
+// so W = I + E with E_ij = B_ij / (B_jj - B_ii) (i != j), and the eigenvalues
+// to second order are B_jj + sum_i B_ij E_ij.  Pairs whose gap is at the
+// rounding level of B are left alone (any basis of a cluster is valid).  The
+// refined eigenvalues replace B's diagonal.  Called by all threads of a warp
+// (sync = __syncwarp) or a CTA (sync = __syncthreads); thread t0 of tn.
+template <typename T, typename Sync>
+__device__ void refine_sweep(T* B, int ldb, T* W, int ldw, int m, int t0, int tn, T* theta, Sync sync) {
+    for (int j = t0; j < m; j += tn) {
+        const T bjj = B[j * ldb + j];
+        T corr = 0;
+        for (int i = 0; i < m; ++i) {
+            T e = 0;
+            if (i != j) {
+                const T bij = B[i * ldb + j], bii = B[i * ldb + i];
+                const T gap = bjj - bii;
+                if (zabs(gap) > T(1e-9) * (zabs(bii) + zabs(bjj)) && zabs(bij) < T(0.25) * zabs(gap)) {
+                    e = bij / gap;
+                    corr += bij * e;
+                }
+            }
+            W[i * ldw + j] = (i == j) ? T(1) : e;
+        }
+        theta[j] = bjj + corr;
+    }
+    sync();
+    for (int j = t0; j < m; j += tn) B[j * ldb + j] = theta[j];
+    sync();
+}
+
 // ---------------------------------------------------------------------------
 // Register-resident warp routines for one 32 x 32 problem per warp: lane l
 // holds column l.  Pairing is the round-robin schedule of rr_pair (index 0

@@ -1030,7 +1030,8 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
                 X[a * ld + c] = d;                        // B
             }
             __syncwarp();
-            warp_jacobi<double>(X, ld, W, ld, m, 4, true, wrd);
+            // one FP64 refinement sweep (closed form: B is diagonal to FP32 rounding)
+            refine_sweep<double>(X, ld, W, ld, m, lane, 32, thd, [] { __syncwarp(); });
             for (int e = lane; e < m * m; e += 32) {
                 const int i = e / m, c = e % m;
                 double d = 0;
