@@ -217,6 +217,25 @@ def union_rows(ts, te):
     return total
 
 
+def measured_traffic(name, units_per_launch):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture (profiles/lift_tc_traffic.json: bytes per output row, scaled by the
+    launch's output rows), or None when no capture covers this kernel or its
+    source has changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "lift_tc_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as fh:
+            cur = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    if rec.get("kernel") != name or rec.get("kernel_source_sha256") != cur:
+        return None
+    return rec["dram_bytes_per_output_row"] * units_per_launch
+
+
 def kernel_model(name, w, launches_per_step, nq_total_rows, union_u_rows):
     """Compulsory bytes per launch of a kernel, for the roofline object."""
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
@@ -345,8 +364,8 @@ def run_gpu(args, w):
         if bound == "hbm":
             ach = units / avg_s / 1e9
             roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-                    "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": measured_traffic(name, out_rows / per_step),
+                    "peak_source": src, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
         else:
             roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                     "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}

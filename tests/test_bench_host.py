@@ -28,3 +28,10 @@ def test_lift_model_counts_writes_and_distinct_reads():
     w = synthetic.WORKLOADS["compress_f32"]
     bound, units = bench.kernel_model("lift", w, 1, 1000, 400)
     assert bound == "hbm" and units == (1000 + 400) * w.k * 4
+
+
+def test_measured_traffic_only_for_the_captured_kernel():
+    assert bench.measured_traffic("sketch", 1000) is None
+    t1 = bench.measured_traffic("lift", 1000)
+    if t1 is not None:               # the capture matches the current kernel source
+        assert abs(bench.measured_traffic("lift", 2000) - 2 * t1) < 1e-6 * t1
