@@ -129,6 +129,14 @@ zs_status zs_store_reset(zs_store* st);
 zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
                         int64_t* factor_bytes);
 
+/* Device fault word of the store (failure detection): 1 once a kernel of
+ * this store gave up a bounded wait on the device (the tensor-core
+ * projection waits on its MMA completions with an iteration limit, then
+ * drains its copies, releases its TMEM and returns, leaving its results
+ * undefined); 0 otherwise.  Synchronises the device.  *flag (host) receives
+ * the word; a non-zero word persists until the store is destroyed.        */
+zs_status zs_store_fault(const zs_store* st, int32_t* flag);
+
 /* Copy block i's stored factors into caller device buffers: U (rows_i x k,
  * ld k), sigma (k), Vt (k x n, ld n), on `stream`.  *rows_i and *k_i (host)
  * receive the block's row count and kept rank min(k, rows_i, n); columns

@@ -114,7 +114,7 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
     if ((s = al(&ews, eig_ws_bytes((int)n, st.fp64, ews_ctas), "eigen workspace")) != ZS_OK) return s;
     if (use_tc_path(st.fp64, (int)n, st.cfg.flags)) {
         const size_t m = tc_width(want_kq, st.tune.eig_m_extra);
-        if ((s = al(&qb, 4 * m * (size_t)n * want_nq, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&qb, 4 * tc_qb_floats((int)m, (int)n) * want_nq, "subspace bases")) != ZS_OK) return s;
         if ((s = al(&ys, 4 * m * (size_t)want_sl * k, "projections")) != ZS_OK) return s;
         aux_tiles = (int64_t)want_sl * k / 128 + want_nq;
         if ((s = al(&aux, tc_aux_bytes(want_nq, aux_tiles, (int)m, want_kq), "Rayleigh-Ritz scratch")) != ZS_OK)
@@ -227,6 +227,8 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.sig = st.sig;
     a.vt = st.vt;
     a.wst = st.w;
+    a.w_rows = st.cap_blocks * st.cfg.k;
+    a.fault = st.d_fault;
     a.b = (int32_t)st.cfg.b;
     a.n = (int32_t)st.cfg.n;
     a.k = st.cfg.k;
@@ -234,6 +236,7 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.kout = kout;
     a.fp64_refine = (st.cfg.flags & ZS_FLAG_FP64_REFINE) ? 1 : 0;
     a.M = x.M;
+    a.m_rows = x.cap_slabs * st.cfg.k;
     a.G = x.G;
     a.sr = x.sr;
     a.vr = x.vr;
@@ -310,17 +313,20 @@ static zs_status store_alloc(zs_store* st) {
     if ((s = al(&st->vt, ts * nb * c.k * c.n, "store V")) != ZS_OK) return s;
     if (use_tc_path(st->fp64, (int)c.n, c.flags))
         if ((s = al(&st->w, ts * nb * c.k * c.n, "store Sigma V^T")) != ZS_OK) return s;
+    if ((s = al((void**)&st->d_fault, sizeof(int), "fault word")) != ZS_OK) return s;
+    ZS_CU(cudaMemset(st->d_fault, 0, sizeof(int)), "memset");
     if ((s = al(&st->tail, st->insize * (size_t)c.b * c.n, "open-block rows")) != ZS_OK) return s;
     // Gram scratch: chunk of blocks whose n x n Grams stay L2-sized
     const size_t gper = ts * (size_t)c.n * c.n;
     const size_t mtc = use_tc_path(st->fp64, (int)c.n, c.flags) ? tc_width(c.k, st->tune.eig_m_extra) : 0;
-    const size_t per_block = gper + 4 * mtc * c.n + 4 * mtc * c.b +
+    const size_t per_block = gper + (mtc ? 4 * tc_qb_floats((int)mtc, (int)c.n) : 0) + 4 * mtc * c.b +
                              (mtc ? 4 * mtc * mtc * ((c.b + 127) / 128 + 1) + 4 * mtc * c.k + 4 * c.k : 0);
     st->gchunk = (int)std::max<size_t>(1, std::min<size_t>(st->gram_budget / per_block, 65535));
     if ((s = al(&st->gscr, gper * st->gchunk, "gram scratch")) != ZS_OK) return s;
     if (use_tc_path(st->fp64, (int)c.n, c.flags)) {
         const size_t m = tc_width(c.k, st->tune.eig_m_extra);
-        if ((s = al(&st->qb, 4 * m * (size_t)c.n * st->gchunk, "subspace bases")) != ZS_OK) return s;
+        if ((s = al(&st->qb, 4 * tc_qb_floats((int)m, (int)c.n) * st->gchunk, "subspace bases")) != ZS_OK)
+            return s;
         if ((s = al(&st->ys, 4 * m * (size_t)c.b * st->gchunk, "projections")) != ZS_OK) return s;
         if ((s = al(&st->aux, tc_aux_bytes(st->gchunk, (int64_t)st->gchunk * ((c.b + 127) / 128), (int)m, c.k),
                     "Rayleigh-Ritz scratch")) != ZS_OK)
@@ -342,7 +348,8 @@ static zs_status store_alloc(zs_store* st) {
             if ((s = al(&ps.G, gper, "append pipeline gram")) != ZS_OK) return s;
             if ((s = al(&ps.ews, eig_ws_bytes((int)c.n, st->fp64, 1), "append pipeline workspace")) != ZS_OK) return s;
             if (mt) {
-                if ((s = al(&ps.qb, 4 * mt * (size_t)c.n, "append pipeline bases")) != ZS_OK) return s;
+                if ((s = al(&ps.qb, 4 * tc_qb_floats((int)mt, (int)c.n), "append pipeline bases")) != ZS_OK)
+                    return s;
                 if ((s = al(&ps.ys, 4 * mt * (size_t)c.b, "append pipeline projections")) != ZS_OK) return s;
                 if ((s = al(&ps.aux, tc_aux_bytes(1, (c.b + 127) / 128, (int)mt, c.k), "append pipeline RR")) != ZS_OK)
                     return s;
@@ -433,7 +440,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     cudaDeviceSynchronize();
     st->qx.release();
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
-    f(st->U); f(st->sig); f(st->vt); f(st->w); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
+    f(st->U); f(st->sig); f(st->vt); f(st->w); if (st->d_fault) cudaFree(st->d_fault); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
     f(st->qb); f(st->ys); f(st->aux);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
@@ -492,9 +499,10 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
             ch.sig = st->sig;
             ch.vt = st->vt;
             ch.w = st->w;
+            ch.fault = st->d_fault;
             ch.ews = st->ews;
             ch.ews_ctas = st->ews_ctas;
-            ch.qb = (char*)st->qb + (size_t)r * sub * 4 * m * c.n;
+            ch.qb = (char*)st->qb + (size_t)r * sub * 4 * tc_qb_floats((int)m, (int)c.n);
             ch.ys = (char*)st->ys + (size_t)r * sub * 4 * m * c.b;
             ch.aux = (char*)st->aux + (size_t)r * st->aux_region;
             cudaError_t e = launch_compress(ch, st->fp64, c.flags, st->tune, st->num_sms, st->cstream[r]);
@@ -525,6 +533,7 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.sig = st->sig;
         ch.vt = st->vt;
         ch.w = st->w;
+        ch.fault = st->d_fault;
         ch.ews = st->ews;
         ch.ews_ctas = st->ews_ctas;
         ch.qb = st->qb;
@@ -686,6 +695,15 @@ extern "C" zs_status zs_store_reset(zs_store* st) {
     }
     st->pending.clear();
     st->T = 0;
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_fault(const zs_store* st, int32_t* flag) {
+    if (!st || !flag) return fail(ZS_EINVAL, "null argument");
+    DeviceGuard g(st->cfg.device);
+    int v = 0;
+    ZS_CU(cudaMemcpy(&v, st->d_fault, sizeof(int), cudaMemcpyDeviceToHost), "fault word");
+    *flag = v;
     return ZS_OK;
 }
 

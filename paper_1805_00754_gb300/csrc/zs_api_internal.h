@@ -64,6 +64,7 @@ struct zs_store {
     void* sig = nullptr;           // cap_blocks x k
     void* vt = nullptr;            // cap_blocks x k x n
     void* w = nullptr;             // tensor path: cap_blocks x k x n, Sigma V^T (the stack-ready slabs)
+    int* d_fault = nullptr;        // device fault word (bounded waits that gave up)
     void* tail = nullptr;          // b x n raw rows of the open block
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace

@@ -16,10 +16,12 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
     sc.m = tc_width(c.k, tu.eig_m_extra);
     sc.power_its = tu.power_its;
     tc_aux_carve(c.aux, c.nblk, (int64_t)c.nblk * ((c.b + 127) / 128), sc.m, c.k, sc);
+    sc.fault = c.fault;
     SrcCompress src{c};
+    const bool aligned = (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) && (c.lda % 4 == 0);
     return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,
                                                  (int64_t)c.nblk * ((c.b + 127) / 128), sc.ews_ctas, num_sms,
-                                                 tu, st);
+                                                 tu, st, aligned);
 }
 
 bool tc_sketch_path(int n, int m, int fused_sketch) { return fused_sketch && sketch_fits(n, m); }

@@ -40,6 +40,7 @@ struct CompressChunk {
     void* qb;         // tensor path: nblk x n x m subspace bases (fp32 holding tf32 values)
     void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
     void* aux;        // tensor path: tc_aux_bytes(nblk, nblk*ceil(b/128), m, k)
+    int* fault;       // device word set to 1 when a bounded wait gives up (or null)
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).
@@ -90,12 +91,14 @@ struct QueryArgs {
     const void* sig;
     const void* vt;
     const void* wst;  // tensor path: store Sigma V^T (interior slabs read from it), or null
+    int64_t w_rows;   // rows allocated behind wst (capacity blocks x k)
     int32_t b, n, k;
     int32_t kq;                   // eigenpairs computed per query (= min(k_out, n))
     int32_t kout;
     int32_t fp64_refine;
     // scratch
     void* M;          // nslab_total * k * n     stacked Sigma_i V_i^T
+    int64_t m_rows;   // rows allocated behind M (slab capacity x k)
     void* G;          // nq * n * n              Gram of M
     void* sr;         // nq * kq                 stitched singular values
     void* vr;         // nq * kq * n             stitched right vectors (transposed)
@@ -107,6 +110,7 @@ struct QueryArgs {
     void* ys;         // tensor path: nslab_total x k x 64 floats (Y = M Q~)
     void* aux;        // tensor path: tc_aux_bytes(nq, aux_tiles, m, kq)
     int64_t aux_tiles;
+    int* fault;       // device word set to 1 when a bounded wait gives up (or null)
 };
 
 // Launch configuration chosen by the autotuner (or defaults).
@@ -119,6 +123,7 @@ struct Tuning {
     int project_ctas_per_sm = 8; // persistent grid of the projection kernel
     int fused_sketch = 1;        // tensor path: sketch kernel (else the bf16 Gram) where it fits
     int pipe_sub_blocks = 0;     // tensor path: blocks per sub-chunk of the two-stream append pipeline (0: off)
+    int tc5_project = 1;         // tensor path: projection on tcgen05 (TMEM accumulator) where it applies
 };
 
 // The tensor-core path (bf16 Gram for the subspace, split-bf16 projection and
@@ -135,6 +140,10 @@ inline int tc_width(int kq, int extra) {
     int m = ((kq + p) + 7) / 8 * 8;
     return m > 64 ? 64 : m;
 }
+// Floats of subspace-basis scratch per item on the tensor path: Q~ (n x m)
+// followed, for the tcgen05 projection, by Q~^T as 32-column chunks in the
+// canonical K-major layout (round16(m) x n).
+inline size_t tc_qb_floats(int m, int n) { return (size_t)(m + (m + 15) / 16 * 16) * n; }
 
 // Launchers (zs_launch_common.cu).  All enqueue on `st` and return cudaError_t of the
 // launch.  `fp64` selects the double-precision instantiation (F64 store).

@@ -4,7 +4,11 @@
 #pragma once
 
 #include <algorithm>
+#include <climits>
+#include <cstring>
 #include <type_traits>
+
+#include <cudaTypedefs.h>
 
 #include "zs_kernels_dev.cuh"
 #include "zs_prof.h"
@@ -93,9 +97,53 @@ static cudaError_t orth_dispatch(const Src& src, const TcScratch& sc, int n, int
                       : orth_launch<Src, 16, 4>(src, sc, n, max_items, st);
 }
 
+// cuTensorMapEncodeTiled from the driver (null where the driver has none)
+static PFN_cuTensorMapEncodeTiled_v12000 t5_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+// rows x n fp32 matrix (row stride ld elements) read in 32 x box_rows boxes, 128-byte swizzle
+static bool t5_map(CUtensorMap* mp, const void* base, int64_t rows, int n, int64_t ld, int box_rows) {
+    const auto fn = t5_encoder();
+    if (!fn || !base || rows < 1 || rows > (int64_t)INT32_MAX) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(mp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+static bool t5_maps(const SrcCompress& s, int n, T5Maps& mp) {
+    return t5_map(&mp.x0, s.c.A, s.c.rows_total, n, s.c.lda, 128);
+}
+// 8-row boxes stay inside one slab when k % 8 == 0
+static bool t5_maps(const SrcQuery& s, int n, T5Maps& mp) {
+    if (s.a.k % 8 != 0) return false;
+    if (!t5_map(&mp.x0, s.a.M, s.a.m_rows, n, n, 8)) return false;
+    return s.a.wst ? t5_map(&mp.x1, s.a.wst, s.a.w_rows, n, n, 8) : t5_map(&mp.x1, s.a.M, s.a.m_rows, n, n, 8);
+}
+
 template <class Src, typename Tin, bool REF, bool QUERY>
-static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int64_t max_tiles,
-                           int ews_ctas, int num_sms, const Tuning& tu, cudaStream_t st) {
+static cudaError_t tc_core(const Src& src, TcScratch sc, int n, int kw, int max_items, int64_t max_tiles,
+                           int ews_ctas, int num_sms, const Tuning& tu, cudaStream_t st, bool rows_aligned16) {
+    // tcgen05 projection (TMA loads): the basis kernels also write Q~^T
+    // (canonical layout) after Q~
+    T5Maps maps;
+    memset(&maps, 0, sizeof maps);
+    const bool t5 = std::is_same<Tin, float>::value && tu.tc5_project && n % 32 == 0 && sc.m <= 64 &&
+                    rows_aligned16 && t5_maps(src, n, maps);
+    sc.Qt = t5 ? sc.Qf + (size_t)max_items * n * sc.m : nullptr;
     const int ntile = (n + 127) / 128;
     const int npairs = ntile * (ntile + 1) / 2;
     const int gi = std::min(max_items, 65535);
@@ -128,7 +176,24 @@ static cudaError_t tc_core(const Src& src, const TcScratch& sc, int n, int kw, i
         }
         ZS_TRY(cudaGetLastError());
     }
-    {
+    if (t5) {
+        // tcgen05 projection: as many CTAs per SM as the stage ring lets fit
+        // (two for m <= 32; TMEM: 256 columns each)
+        const size_t sm = t5_smem_bytes(sc.m);
+        ZS_TRY(set_smem(k_project_tc5<Src>, sm));
+        ZS_TRY(cudaFuncSetAttribute(k_project_tc5<Src>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
+        prof::Scope ps(QUERY ? "project_query" : "project", st);
+        // CTAs per SM: shared memory (with the per-block reservation) and TMEM
+        // (512 columns per SM); registers (< 128 per thread) are not binding
+        int dev = 0, smem_sm = 0, resv = 0;
+        ZS_TRY(cudaGetDevice(&dev));
+        ZS_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        ZS_TRY(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int per_sm = std::max(1, std::min(smem_sm / (int)(sm + resv), (int)(512 / kT5Cols)));
+        const int gp = (int)std::min<int64_t>(max_tiles, (int64_t)num_sms * per_sm);
+        k_project_tc5<Src><<<std::max(gp, 1), kT5Threads, sm, st>>>(src, sc, n, maps);
+    } else {
         const size_t sm = project_smem_bytes(sc.m);
         ZS_TRY(set_smem(k_project<Src, Tin>, sm));
         prof::Scope ps(QUERY ? "project_query" : "project", st);
@@ -241,9 +306,11 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             sc.m = tc_width(kq, tu.eig_m_extra);
             sc.power_its = tu.power_its;
             tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
+            sc.fault = a.fault;
             SrcQuery src{a};
+            // stacked rows (M and the store's Sigma V^T) are 16-byte aligned when n % 4 == 0
             ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
-                                                        tu, st)));
+                                                        tu, st, n % 4 == 0)));
             {
                 const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
                 ZS_TRY(set_smem(k_bfix, sm));

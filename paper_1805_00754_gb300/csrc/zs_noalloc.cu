@@ -92,7 +92,7 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         ews_bytes = (zs::eig_ws_bytes((int)n, fp64, ews_ctas) + 255) & ~(size_t)255;
     }
     auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t qper = r256(4 * mt * (size_t)n);
+    const size_t qper = tc ? r256(4 * zs::tc_qb_floats((int)mt, (int)n)) : 0;
     const size_t proj = r256(4 * mt * (size_t)b);
     // Rayleigh-Ritz scratch of one block (tile partials, Q~^T Q~, Ritz data) with slack for alignment
     const size_t auxp = tc ? r256(4 * mt * mt * ((b + 127) / 128 + 1) + 4 * mt * k + 4 * k + 1024) : 0;

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "zs_internal.h"
@@ -115,6 +116,7 @@ struct SrcQuery {
 struct TcScratch {
     float* G;               // items x n x n
     float* Qf;              // items x n x m: Q~, values exact in tf32
+    float* Qt;              // items x round16(m) x n: Q~^T for the tcgen05 projection (or null)
     float* Y;               // (sum of rows) x m, row offsets from Src::ybase
     void* ews;              // per-CTA workspace (subspace Y block), ews_ctas x n x (m+1) floats
     int ews_ctas;
@@ -124,6 +126,7 @@ struct TcScratch {
     float* Cq;              // items x m x m: Q~^T Q~
     float* Zs;              // items x m x kw: Ritz coefficients
     float* th;              // items x kw: Ritz values (sigma^2)
+    int* fault;             // set to 1 by a kernel whose bounded wait gave up (or null)
 };
 
 template <typename Tin>
@@ -333,6 +336,14 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
             Q[i * ldq + c] = h;                         // Q~ as it will be used
         }
         __syncthreads();
+        if (sc.Qt) {
+            const int np = (m + 15) / 16 * 16;
+            float* Qt = sc.Qt + (size_t)item * np * n;
+            for (int e = tid; e < n * np; e += nt) {
+                const int i = e / np, c = e - (e / np) * np;
+                Qt[(size_t)(i >> 5) * np * 32 + tc5_canon(c, i & 31, 32)] = c < m ? Q[i * ldq + c] : 0.f;
+            }
+        }
         // C = Q~^T Q~ (exact products of bf16 values, fp32 sums)
         float* Cq = sc.Cq + (size_t)item * m * m;
         for (int e = tid; e < m * m; e += nt) {
@@ -537,6 +548,328 @@ __global__ void __launch_bounds__(256, 3) k_project(Src src, TcScratch sc, int n
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// 3'. Y = X Q~ on Blackwell tensor cores (tcgen05, kind::tf32, accumulator in
+//     TMEM), float inputs with n % 32 == 0, warp-specialised.  A CTA walks its
+//     128-row tiles (tile row r <-> TMEM lane r) as one stream of 32-column
+//     chunks through a ring of kT5Stages shared-memory stages:
+//       warp 5 (loads)  X by TMA into the 128-byte swizzled K-major layout
+//                       (one 128-row box, or 8-row boxes that follow a query's
+//                       row sources) and the chunk of Q~^T - stored by the
+//                       basis kernel in the canonical K-major layout - by one
+//                       bulk copy, both completing on the stage's mbarrier;
+//       warps 0-3       one tile row per thread: X_lo = X - tf32(X) in
+//                       registers (zero past the item) into one of two TMEM
+//                       buffers; at a tile's end the epilogue (one Y row per
+//                       thread from TMEM, the tile's Y^T Y on mma.sync tensor
+//                       cores as in k_project);
+//       warp 4, lane 0  the MMAs: Y += X_hi Q~ with A = X from shared memory
+//                       (the tensor core reads it as tf32, dropping the 13
+//                       low mantissa bits: X_hi with no work) and Y += X_lo Q~
+//                       with A from TMEM - FP32 accuracy from eight MMAs of
+//                       K = 8 per chunk, into one of two TMEM accumulators so
+//                       the next tile's MMAs need not wait for the epilogue.
+//     The roles hand over through mbarriers only.  A tf32 MMA of M = 128
+//     costs about the same for any N <= 128, so with N = m the tensor pipe sets
+//     the pace; two CTAs per SM keep it fed.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int kT5Stages = 4;
+constexpr int kT5MaxPoll = 1 << 20;
+constexpr int kT5Threads = 192;
+// Tensor maps of the row sources (32 x 128 or 32 x 8 float boxes, 128-byte
+// swizzle): SrcCompress reads x0 (the chunk's rows); SrcQuery reads x0 (the
+// stacked M) and x1 (the store's Sigma V^T).
+struct alignas(128) T5Maps {
+    CUtensorMap x0, x1;
+};
+__host__ __device__ __forceinline__ int t5_np(int m) { return (m + 15) / 16 * 16; }      // MMA N
+__host__ __device__ __forceinline__ uint32_t t5_stage_bytes(int m) { return 128 * 128 + t5_np(m) * 128; }
+__host__ __device__ __forceinline__ uint32_t t5_ys_bytes(int m) {   // the epilogue's Y tile
+    return (128 * pj_ldq(m) * 4 + 1023) / 1024 * 1024;
+}
+__host__ __device__ __forceinline__ size_t t5_smem_bytes(int m) {
+    return (size_t)kT5Stages * t5_stage_bytes(m) + t5_ys_bytes(m) + 8 * (2 * kT5Stages + 6) + 16;
+}
+// TMEM columns: accumulators (np <= 64) at 0 and 64, X_lo buffers at 128 and 160
+constexpr uint32_t kT5Cols = 256;
+
+template <class Src>
+__global__ void __launch_bounds__(kT5Threads, 1) k_project_tc5(Src src, TcScratch sc, int n,
+                                                            const __grid_constant__ T5Maps maps) {
+    extern __shared__ __align__(1024) unsigned char t5raw[];
+    const int m = sc.m, np = t5_np(m), ldq = pj_ldq(m), ntn = m / 8, mp = (m + 15) / 16 * 16;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t stb = t5_stage_bytes(m);
+    float* Ys = reinterpret_cast<float*>(t5raw + kT5Stages * stb);   // 128 x ldq
+    uint64_t* full = reinterpret_cast<uint64_t*>(t5raw + kT5Stages * stb + t5_ys_bytes(m));
+    uint64_t* done = full + kT5Stages;      // the MMAs of the stage's chunk have completed
+    uint64_t* lo_ready = done + kT5Stages;  // [2] X_lo of a chunk is in TMEM (4 warp arrivals)
+    uint64_t* acc_full = lo_ready + 2;      // [2] the tile's accumulator is complete
+    uint64_t* acc_empty = acc_full + 2;     // [2] the epilogue has read the accumulator (4 warp arrivals)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    if (smem_u32(t5raw) & 1023) {           // the swizzle atoms need a 1024-byte aligned base
+        if (tid == 0 && sc.fault) atomicExch(sc.fault, 1);
+        return;
+    }
+    if (warp == 0) tc5_alloc(tmem_slot, kT5Cols);
+    if (tid == 0) {
+        for (int q = 0; q < kT5Stages; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&done[q], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&lo_ready[i], 4);
+            mbar_init(&acc_full[i], 1);
+            mbar_init(&acc_empty[i], 4);
+        }
+    }
+    fence_proxy_async();
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nch = n / 32;
+    const int64_t ntiles = src.ntiles();
+    // the CTA's tiles, those without rows skipped
+    auto next_tile = [&](int64_t t) {
+        for (; t < ntiles; t += gridDim.x) {
+            int item, rt;
+            src.tile_item(t, item, rt);
+            if (rt * 128 < src.rows(item)) break;
+        }
+        return t;
+    };
+    bool ok = true;                         // after a failed wait no further waits: the roles run out quickly
+    int64_t last_commit = -1;               // MMA thread: the last chunk it committed
+    int64_t issued = 0;                     // load warp: chunks issued
+    if (warp == 5) {
+        // ---------------- loads
+        int64_t q = 0;
+        for (int64_t tile = next_tile(blockIdx.x); tile < ntiles; tile = next_tile(tile + gridDim.x)) {
+            int item, rt;
+            src.tile_item(tile, item, rt);
+            const int r0 = rt * 128, valid = min(128, src.rows(item) - r0);
+            const float* qt = sc.Qt + (size_t)item * np * n;
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int s = (int)(q % kT5Stages);
+                // the stage's previous chunk (q - stages) has been read by its MMAs
+                if (ok && q >= kT5Stages &&
+                    !mbar_wait(&done[s], (uint32_t)((q - kT5Stages) / kT5Stages) & 1, kT5MaxPoll))
+                    ok = false;
+                unsigned char* Xs = t5raw + (size_t)s * stb;
+                const uint32_t bbytes = (uint32_t)np * 128;
+                const float* bsrc = qt + (size_t)c * np * 32;
+                if constexpr (std::is_same<Src, SrcCompress>::value) {
+                    if (lane == 0) {
+                        mbar_expect_tx(&full[s], 128 * 128 + bbytes);
+                        tma_load_2d(Xs, &maps.x0, c * 32, (int)((int64_t)item * src.c.b + r0), &full[s]);
+                        bulk_load(Xs + 128 * 128, bsrc, bbytes, &full[s]);
+                    }
+                } else {
+                    // 8-row boxes (k % 8 == 0: a box lies in one slab); interior
+                    // slabs from the store's Sigma V^T, the boundary slabs from M
+                    const QPlan& P = src.a.plans[item];
+                    const int kk = src.a.k;
+                    const uint32_t kmagic = (uint32_t)((0x100000000ull + (uint64_t)kk - 1) / (uint64_t)kk);
+                    const int npc = (valid + 7) / 8;
+                    if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)npc * 1024 + bbytes);
+                    __syncwarp();
+                    if (lane < npc) {
+                        const int r = r0 + 8 * lane;
+                        const int t = (int)__umulhi((uint32_t)r, kmagic);
+                        const bool inner = src.a.wst && t > 0 && t < P.nslab - 1;
+                        const int y = inner ? (int)(P.S * kk + r) : (int)(P.slab0 * kk + r);
+                        tma_load_2d(Xs + lane * 1024, inner ? (const void*)&maps.x1 : (const void*)&maps.x0, c * 32,
+                                    y, &full[s]);
+                    }
+                    if (lane == 31) bulk_load(Xs + 128 * 128, bsrc, bbytes, &full[s]);
+                }
+                issued = q + 1;
+            }
+        }
+    } else if (warp == 4) {
+        // ---------------- MMAs (one thread)
+        if (lane == 0) {
+            const uint32_t idesc = tc5_idesc_tf32(128, np);
+            int64_t q = 0, t = 0;
+            for (int64_t tile = next_tile(blockIdx.x); tile < ntiles; tile = next_tile(tile + gridDim.x), ++t) {
+                const int a = (int)(t & 1);
+                const uint32_t acc = tmem + 64 * a;
+                // the epilogue of tile t - 2 has read this accumulator
+                if (ok && t >= 2 && !mbar_wait(&acc_empty[a], (uint32_t)((t - 2) / 2) & 1, kT5MaxPoll)) ok = false;
+                for (int c = 0; c < nch; ++c, ++q) {
+                    const int s = (int)(q % kT5Stages), b = (int)(q & 1);
+                    if (ok && !mbar_wait(&full[s], (uint32_t)(q / kT5Stages) & 1, kT5MaxPoll)) ok = false;
+                    if (ok && !mbar_wait(&lo_ready[b], (uint32_t)(q / 2) & 1, kT5MaxPoll)) ok = false;
+                    tc5_fence_after();
+                    if (!ok) continue;
+                    const uint32_t xa = smem_u32(t5raw + (size_t)s * stb), ba = xa + 128 * 128;
+                    const uint32_t la = tmem + 128 + 32 * b;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        tc5_mma_tf32(acc, tc5_desc_sw128(xa + ks * 32), tc5_desc(ba + ks * 256, 128, 1024), idesc,
+                                     (c > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        tc5_mma_tf32_ta(acc, la + ks * 8, tc5_desc(ba + ks * 256, 128, 1024), idesc, 1u);
+                    tc5_commit(&done[s]);
+                    last_commit = q;
+                    if (c == nch - 1) tc5_commit(&acc_full[a]);
+                }
+            }
+        }
+    } else {
+        // ---------------- X_lo and the epilogue (warps 0-3, thread = tile row).
+        // A tile's epilogue runs once X_lo of the next tile's first two chunks
+        // is in TMEM, so the MMAs have work while it runs.
+        const int row = tid, g = lane >> 2, t4 = lane & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        bool pending = false;               // a finished tile waits for its epilogue
+        int64_t e_tile = 0, e_t = 0;
+        int e_item = 0, e_r0 = 0, e_valid = 0;
+        auto epilogue = [&]() {
+            const int a = (int)(e_t & 1);
+            if (ok && !mbar_wait(&acc_full[a], (uint32_t)(e_t / 2) & 1, kT5MaxPoll)) ok = false;
+            tc5_fence_after();
+            float y0[32], y1[32];
+            tc5_ld32(lane_base + 64 * a, y0);
+            if (np > 32) tc5_ld32(lane_base + 64 * a + 32, y1);
+            else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) y1[i] = 0.f;
+            }
+            tc5_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[a]);
+            // Ys: 128 x ldq, zero past the item and column m
+            const bool live = row < e_valid;
+#pragma unroll
+            for (int c4 = 0; c4 < 16; ++c4) {
+                if (4 * c4 >= mp) break;
+                float4 v = c4 < 8 ? make_float4(y0[4 * c4], y0[4 * c4 + 1], y0[4 * c4 + 2], y0[4 * c4 + 3])
+                                  : make_float4(y1[4 * c4 - 32], y1[4 * c4 - 31], y1[4 * c4 - 30], y1[4 * c4 - 29]);
+                if (4 * c4 >= m || !live) v = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4*>(Ys + row * ldq + 4 * c4) = v;
+            }
+            named_sync(1, 128);
+            // the tile's Y rows, coalesced (16-byte pieces, consecutive threads on consecutive pieces)
+            {
+                float* Y = sc.Y + ((size_t)src.ybase(e_item) + e_r0) * m;
+                const int pr = m / 4;       // pieces per row
+                for (int p = tid; p < e_valid * pr; p += 128) {
+                    const int r = p / pr, c4 = p - (p / pr) * pr;
+                    *reinterpret_cast<float4*>(Y + (size_t)r * m + 4 * c4) =
+                        *reinterpret_cast<const float4*>(Ys + r * ldq + 4 * c4);
+                }
+            }
+            // this tile's Y^T Y on tensor cores (two tf32 terms, three products),
+            // fixed order; two output tiles per pass give two independent chains
+            float* Hp = sc.Hp + (size_t)e_tile * m * m;
+            const int nmt = mp / 16, tot = nmt * ntn;
+            for (int o0 = warp; o0 < tot; o0 += 8) {
+                const bool two = o0 + 4 < tot;
+                float h[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+                for (int k0 = 0; k0 < 128; k0 += 8) {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        if (u == 1 && !two) continue;
+                        const int ot = o0 + 4 * u;
+                        const int mt = ot / ntn, nt = ot - (ot / ntn) * ntn;
+                        const float* ya = Ys + (k0 + t4) * ldq + mt * 16 + g;
+                        const float* yb = Ys + (k0 + t4) * ldq + nt * 8 + g;
+                        uint32_t ah0, al0, ah1, al1, ah2, al2, ah3, al3, bh0, bl0, bh1, bl1;
+                        tf32_split(ya[0], ah0, al0);
+                        tf32_split(ya[8], ah1, al1);
+                        tf32_split(ya[4 * ldq], ah2, al2);
+                        tf32_split(ya[4 * ldq + 8], ah3, al3);
+                        tf32_split(yb[0], bh0, bl0);
+                        tf32_split(yb[4 * ldq], bh1, bl1);
+                        mma_tf32(h[u], al0, al1, al2, al3, bh0, bh1);
+                        mma_tf32(h[u], ah0, ah1, ah2, ah3, bl0, bl1);
+                        mma_tf32(h[u], ah0, ah1, ah2, ah3, bh0, bh1);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (u == 1 && !two) continue;
+                    const int ot = o0 + 4 * u;
+                    const int mt = ot / ntn, nt = ot - (ot / ntn) * ntn;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int i = mt * 16 + g + ((e >> 1) ? 8 : 0);
+                        const int j = nt * 8 + 2 * t4 + (e & 1);
+                        if (i < m) Hp[i * m + j] = h[u][e];
+                    }
+                }
+            }
+            named_sync(1, 128);             // Ys is rewritten by the next epilogue
+            pending = false;
+        };
+        int64_t q = 0, t = 0;
+        for (int64_t tile = next_tile(blockIdx.x); tile < ntiles; tile = next_tile(tile + gridDim.x), ++t) {
+            int item, rt;
+            src.tile_item(tile, item, rt);
+            const int r0 = rt * 128, valid = min(128, src.rows(item) - r0);
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int s = (int)(q % kT5Stages), b = (int)(q & 1);
+                if (ok && !mbar_wait(&full[s], (uint32_t)(q / kT5Stages) & 1, kT5MaxPoll)) ok = false;
+                // the MMAs of chunk q - 2 have read this X_lo buffer
+                if (ok && q >= 2 &&
+                    !mbar_wait(&done[(q - 2) % kT5Stages], (uint32_t)((q - 2) / kT5Stages) & 1, kT5MaxPoll))
+                    ok = false;
+                tc5_fence_after();
+                // this thread's row: its 16-byte pieces sit at j ^ (row % 8) (128-byte swizzle)
+                float* xr = reinterpret_cast<float*>(t5raw + (size_t)s * stb) + row * 32;
+                float lo[32];
+                if (row < valid) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 v = *reinterpret_cast<const float4*>(xr + 4 * (j ^ (row & 7)));
+                        lo[4 * j] = v.x - __uint_as_float(__float_as_uint(v.x) & 0xffffe000u);
+                        lo[4 * j + 1] = v.y - __uint_as_float(__float_as_uint(v.y) & 0xffffe000u);
+                        lo[4 * j + 2] = v.z - __uint_as_float(__float_as_uint(v.z) & 0xffffe000u);
+                        lo[4 * j + 3] = v.w - __uint_as_float(__float_as_uint(v.w) & 0xffffe000u);
+                    }
+                } else {                    // past the item: zero in both terms
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4*>(xr + 4 * j) = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) lo[j] = 0.f;
+                }
+                tc5_st32(lane_base + 128 + 32 * b, lo);
+                fence_proxy_async();
+                tc5_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&lo_ready[b]);
+                if (pending && c == (nch > 1 ? 1 : 0)) epilogue();
+            }
+            pending = true;
+            e_tile = tile;
+            e_t = t;
+            e_item = item;
+            e_r0 = r0;
+            e_valid = valid;
+        }
+        if (pending) epilogue();
+    }
+    if (__syncthreads_or(!ok)) {
+        // a wait gave up: let the MMAs (the last commit tracks all of them)
+        // and the copies already issued finish, bounded, before the
+        // accumulators and the shared memory are released
+        if (warp == 4 && lane == 0 && last_commit >= 0)
+            mbar_wait(&done[last_commit % kT5Stages], (uint32_t)(last_commit / kT5Stages) & 1, kT5MaxPoll);
+        if (warp == 5 && lane == 0)
+            for (int64_t c = issued > kT5Stages ? issued - kT5Stages : 0; c < issued; ++c)
+                mbar_wait(&full[c % kT5Stages], (uint32_t)(c / kT5Stages) & 1, kT5MaxPoll);
+        if (tid == 0 && sc.fault) atomicExch(sc.fault, 1);
+    }
+    tc5_fence_before();
+    __syncthreads();
+    tc5_fence_after();
+    if (warp == 0) tc5_dealloc(tmem, kT5Cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -883,10 +1216,19 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
     }
     // Q~ = tf32(Q): to the projection's scratch and, for C, to shared memory
     float* Qf = sc.Qf + (size_t)item * n * m;
+    const int np = (m + 15) / 16 * 16;
+    float* Qt = sc.Qt ? sc.Qt + (size_t)item * np * n : nullptr;
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
         const int col = warp + kOrthWarps * j;
-        if (col >= m) continue;
+        if (col >= m) {
+            // zero columns m..round16(m) of the transposed copy (MMA N padding)
+            if (Qt && col < np)
+#pragma unroll
+                for (int r = 0; r < RPL; ++r)
+                    if (lane + 32 * r < n) Qt[(size_t)r * np * 32 + tc5_canon(col, lane, 32)] = 0.f;
+            continue;
+        }
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int row = lane + 32 * r;
@@ -894,6 +1236,8 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
             if (row < n) {
                 Qf[(size_t)row * m + col] = s[j][r];
                 osm[row * lds + col] = s[j][r];
+                // Q~^T, 32-row chunk r, canonical K-major position (col, lane)
+                if (Qt) Qt[(size_t)r * np * 32 + tc5_canon(col, lane, 32)] = s[j][r];
             }
         }
     }

@@ -59,6 +59,7 @@ SIGNATURES = {
     "zs_store_append": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
     "zs_store_reset": (C.c_int, [C.c_void_p]),
     "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "zs_store_fault": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "zs_store_export_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
     "zs_compress_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int64, C.c_int64,
@@ -188,6 +189,12 @@ class Store:
         T, nb, by = C.c_int64(), C.c_int64(), C.c_int64()
         _check(lib().zs_store_info(self._h, C.byref(T), C.byref(nb), C.byref(by)))
         return T.value, nb.value, by.value
+
+    def fault(self) -> int:
+        """The store's device fault word: 1 once a kernel gave up a bounded wait."""
+        f = C.c_int32()
+        _check(lib().zs_store_fault(self._h, C.byref(f)))
+        return f.value
 
     def export_block(self, i: int, stream=None):
         U = torch.empty((self.b, self.k), dtype=self.fdtype, device=self.device)
