@@ -1671,12 +1671,13 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
 // ---------------------------------------------------------------------------
 // 5. Lift on tf32 tensor cores (float stores): the rows of U_{S:E} are the
 //    stored U_i rows times each slab's coefficients C (k x kq) (Algorithm 2,
-//    last step; Eq. 9), one warp per slab, 16 rows per step.  U rows and C are
+//    last step; Eq. 9), one warp per slab, 32 rows per step.  U rows and C are
 //    split into two tf32 terms each (three products: FP32-grade results); C is
 //    split once per slab into two shared tiles.
 // ---------------------------------------------------------------------------
 template <int QMAX>
-__host__ __device__ constexpr int lift_ldc() { return (QMAX + 31) / 32 * 32 + 8; }
+// C tile row stride: 4 * LDC = 8 (mod 32) keeps the permuted B loads (rows 4 t4 + .., column g) on distinct banks
+__host__ __device__ constexpr int lift_ldc() { return (QMAX + 31) / 32 * 32 + 2; }
 template <int KMAX, int QMAX>
 __host__ __device__ __forceinline__ size_t lift_tc_warp_floats() { return (size_t)2 * KMAX * lift_ldc<QMAX>(); }
 
@@ -1691,7 +1692,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
     float* Cl = Ch + KMAX * LDC;
     const int nq = a.hdr->nq;
     const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
-    const int nkt = (k + 7) / 8, nnt = (kout + 7) / 8;
+    const int nnt = (kout + 7) / 8;
     // each warp takes a contiguous range of slabs, so the owning query only
     // advances (one search per warp instead of one per slab)
     const int64_t nw = (int64_t)gridDim.x * wpc, wid = (int64_t)blockIdx.x * wpc + warp;
@@ -1718,70 +1719,143 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
         float* out = (float*)P.U;
         const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
         const bool pair = (kout % 2 == 0) && (P.ldu % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
-        // U fragments of the next 16-row step are loaded before the current
-        // step's products (software pipeline over the slab's rows)
-        float nx[KMAX / 8][4];
-        auto fetch = [&](int r0, float (&dst)[KMAX / 8][4]) {
+        // The MMA's K order is permuted so that each thread reads its U row
+        // segments as 16-byte pieces: in column group gi (16 columns), thread
+        // t4 holds columns 16 gi + 4 t4 + {0, 1} as K slots (t4, t4 + 4) of
+        // step 2 gi and + {2, 3} as those of step 2 gi + 1; the B fragments
+        // take C's rows in the same order.  32 rows per step, the next 32
+        // prefetched (two 16-row halves).
+        constexpr int NG = KMAX / 16;
+        const int ngv = (k + 15) / 16;
+        const bool vec = (k % 4) == 0;      // 16-byte aligned row segments
+        float nx[2][NG][2][4];
+        auto fetch = [&](int r0, float (&dst)[NG][2][4]) {
             const int ra = r0 + g, rb = r0 + g + 8;
             const bool va = ra < br.hi, vb = rb < br.hi;
             const float* pa = U + (int64_t)ra * k;
             const float* pb = U + (int64_t)rb * k;
 #pragma unroll
-            for (int kt = 0; kt < KMAX / 8; ++kt) {
-                const int c0 = kt * 8 + t4, c1 = c0 + 4;
-                dst[kt][0] = (kt < nkt && va && c0 < k) ? __ldg(pa + c0) : 0.f;
-                dst[kt][1] = (kt < nkt && vb && c0 < k) ? __ldg(pb + c0) : 0.f;
-                dst[kt][2] = (kt < nkt && va && c1 < k) ? __ldg(pa + c1) : 0.f;
-                dst[kt][3] = (kt < nkt && vb && c1 < k) ? __ldg(pb + c1) : 0.f;
+            for (int gi = 0; gi < NG; ++gi) {
+                const int c = gi * 16 + 4 * t4;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+                if (gi < ngv) {
+                    if (vec) {
+                        if (va && c < k) x = __ldg(reinterpret_cast<const float4*>(pa + c));
+                        if (vb && c < k) y = __ldg(reinterpret_cast<const float4*>(pb + c));
+                    } else {
+                        if (va) {
+                            x.x = c < k ? __ldg(pa + c) : 0.f;
+                            x.y = c + 1 < k ? __ldg(pa + c + 1) : 0.f;
+                            x.z = c + 2 < k ? __ldg(pa + c + 2) : 0.f;
+                            x.w = c + 3 < k ? __ldg(pa + c + 3) : 0.f;
+                        }
+                        if (vb) {
+                            y.x = c < k ? __ldg(pb + c) : 0.f;
+                            y.y = c + 1 < k ? __ldg(pb + c + 1) : 0.f;
+                            y.z = c + 2 < k ? __ldg(pb + c + 2) : 0.f;
+                            y.w = c + 3 < k ? __ldg(pb + c + 3) : 0.f;
+                        }
+                    }
+                }
+                // fragment order a0 (row g, slot t4), a1 (row g+8, slot t4), a2 (row g, slot t4+4), a3
+                dst[gi][0][0] = x.x; dst[gi][0][1] = y.x; dst[gi][0][2] = x.y; dst[gi][0][3] = y.y;
+                dst[gi][1][0] = x.z; dst[gi][1][1] = y.z; dst[gi][1][2] = x.w; dst[gi][1][3] = y.w;
             }
         };
-        if (br.lo < br.hi) fetch(br.lo, nx);
-        for (int r0 = br.lo; r0 < br.hi; r0 += 16) {
-            float cx[KMAX / 8][4];
+        if (br.lo < br.hi) {
+            fetch(br.lo, nx[0]);
+            fetch(br.lo + 16, nx[1]);
+        }
+        // B fragments of the slab (fixed over its rows) held in registers when they fit
+        constexpr bool HOIST = NG * (QMAX / 8) <= 4;
+        uint32_t bf[HOIST ? NG : 1][2][HOIST ? QMAX / 8 : 1][4];
+        if constexpr (HOIST) {
 #pragma unroll
-            for (int kt = 0; kt < KMAX / 8; ++kt)
+            for (int gi = 0; gi < NG; ++gi)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) cx[kt][e] = nx[kt][e];
-            if (r0 + 16 < br.hi) fetch(r0 + 16, nx);
-            float acc[QMAX / 8][4];
+                for (int j = 0; j < 2; ++j) {
+                    const int cr = gi * 16 + 4 * t4 + 2 * j;
 #pragma unroll
-            for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
-            const int ra = r0 + g, rb = r0 + g + 8;
+                    for (int nt = 0; nt < QMAX / 8; ++nt) {
+                        bf[gi][j][nt][0] = __float_as_uint(Ch[cr * LDC + nt * 8 + g]);
+                        bf[gi][j][nt][1] = __float_as_uint(Ch[(cr + 1) * LDC + nt * 8 + g]);
+                        bf[gi][j][nt][2] = __float_as_uint(Cl[cr * LDC + nt * 8 + g]);
+                        bf[gi][j][nt][3] = __float_as_uint(Cl[(cr + 1) * LDC + nt * 8 + g]);
+                    }
+                }
+        }
+        for (int r0 = br.lo; r0 < br.hi; r0 += 32) {
+            float cx[2][NG][2][4];
 #pragma unroll
-            for (int kt = 0; kt < KMAX / 8; ++kt) {
-                if (kt >= nkt) break;
-                const int c0 = kt * 8 + t4;
-                uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-                tf32_split_trunc(cx[kt][0], h0, l0);
-                tf32_split_trunc(cx[kt][1], h1, l1);
-                tf32_split_trunc(cx[kt][2], h2, l2);
-                tf32_split_trunc(cx[kt][3], h3, l3);
-                const float* bh = Ch + c0 * LDC + g;
-                const float* bl = Cl + c0 * LDC + g;
+            for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                for (int gi = 0; gi < NG; ++gi)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) cx[h2][gi][j][e] = nx[h2][gi][j][e];
+            if (r0 + 32 < br.hi) {
+                fetch(r0 + 32, nx[0]);
+                fetch(r0 + 48, nx[1]);
+            }
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int rs = r0 + 16 * h2;
+                if (rs >= br.hi) break;
+                float acc[QMAX / 8][4];
+#pragma unroll
+                for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+#pragma unroll
+                for (int gi = 0; gi < NG; ++gi) {
+                    if (gi >= ngv) break;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        uint32_t h0, h1, h2v, h3, l0, l1, l2, l3;
+                        tf32_split_trunc(cx[h2][gi][j][0], h0, l0);
+                        tf32_split_trunc(cx[h2][gi][j][1], h1, l1);
+                        tf32_split_trunc(cx[h2][gi][j][2], h2v, l2);
+                        tf32_split_trunc(cx[h2][gi][j][3], h3, l3);
+                        // K slot t4 <-> C row 16 gi + 4 t4 + 2 j, slot t4 + 4 <-> the row after it
+                        const int cr = gi * 16 + 4 * t4 + 2 * j;
+                        const float* bh = Ch + cr * LDC + g;
+                        const float* bl = Cl + cr * LDC + g;
+#pragma unroll
+                        for (int nt = 0; nt < QMAX / 8; ++nt) {
+                            if (nt >= nnt) break;
+                            uint32_t bh0, bh1, bl0, bl1;
+                            if constexpr (HOIST) {
+                                bh0 = bf[gi][j][nt][0];
+                                bh1 = bf[gi][j][nt][1];
+                                bl0 = bf[gi][j][nt][2];
+                                bl1 = bf[gi][j][nt][3];
+                            } else {
+                                bh0 = __float_as_uint(bh[nt * 8]);
+                                bh1 = __float_as_uint(bh[LDC + nt * 8]);
+                                bl0 = __float_as_uint(bl[nt * 8]);
+                                bl1 = __float_as_uint(bl[LDC + nt * 8]);
+                            }
+                            mma_tf32(acc[nt], l0, l1, l2, l3, bh0, bh1);
+                            mma_tf32(acc[nt], h0, h1, h2v, h3, bl0, bl1);
+                            mma_tf32(acc[nt], h0, h1, h2v, h3, bh0, bh1);
+                        }
+                    }
+                }
+                const int ra = rs + g, rb = rs + g + 8;
 #pragma unroll
                 for (int nt = 0; nt < QMAX / 8; ++nt) {
                     if (nt >= nnt) break;
-                    const uint32_t bh0 = __float_as_uint(bh[nt * 8]), bh1 = __float_as_uint(bh[4 * LDC + nt * 8]);
-                    const uint32_t bl0 = __float_as_uint(bl[nt * 8]), bl1 = __float_as_uint(bl[4 * LDC + nt * 8]);
-                    mma_tf32(acc[nt], l0, l1, l2, l3, bh0, bh1);
-                    mma_tf32(acc[nt], h0, h1, h2, h3, bl0, bl1);
-                    mma_tf32(acc[nt], h0, h1, h2, h3, bh0, bh1);
-                }
-            }
+                    const int c = nt * 8 + 2 * t4;
 #pragma unroll
-            for (int nt = 0; nt < QMAX / 8; ++nt) {
-                if (nt >= nnt) break;
-                const int c = nt * 8 + 2 * t4;
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int r = hh ? rb : ra;
-                    if (r >= br.hi || c >= kout) continue;
-                    float* orow = out + (o0 + r) * P.ldu + c;
-                    if (pair) {
-                        *reinterpret_cast<float2*>(orow) = make_float2(acc[nt][2 * hh], acc[nt][2 * hh + 1]);
-                    } else {
-                        orow[0] = acc[nt][2 * hh];
-                        if (c + 1 < kout) orow[1] = acc[nt][2 * hh + 1];
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int r = hh ? rb : ra;
+                        if (r >= br.hi || c >= kout) continue;
+                        float* orow = out + (o0 + r) * P.ldu + c;
+                        if (pair) {
+                            *reinterpret_cast<float2*>(orow) = make_float2(acc[nt][2 * hh], acc[nt][2 * hh + 1]);
+                        } else {
+                            orow[0] = acc[nt][2 * hh];
+                            if (c + 1 < kout) orow[1] = acc[nt][2 * hh + 1];
+                        }
                     }
                 }
             }

@@ -229,6 +229,7 @@ def test_f32_compress_workload(refine):
         out = st.query(int(a), int(z))
         torch.cuda.synchronize()
         compare_query(out, oracle.query(ost, int(a), int(z)), **F32, label=f"f32 [{a},{z}]")
+    assert st.fault() == 0          # no bounded wait of the tensor-core kernels gave up
 
 
 def test_exact_gram_path_matches_oracle_and_tensor_path():
@@ -272,6 +273,7 @@ def test_ragged_batch_f32():
         compare_query(outs[q], ref, **F32, label=f"ragged {q}")
         worst = max(worst, sigma_rel_err(outs[q], ref))
     assert worst <= 1e-4
+    assert st.fault() == 0
 
 
 def test_serving_results_equal_alone():
