@@ -1152,6 +1152,12 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
     const int item = blockIdx.x;
     if (item >= src.count()) return;
     const float* Sg = sc.G + (size_t)item * n * m;
+    // S through shared memory: coalesced reads of its rows, then columns per lane
+    for (int e = threadIdx.x; e < n * m; e += 32 * kOrthWarps) {
+        const int row = e / m, col = e - (e / m) * m;
+        osm[row * lds + col] = Sg[e];
+    }
+    __syncthreads();
     float s[CPW][RPL], nrm0[CPW];
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
@@ -1160,11 +1166,12 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int row = lane + 32 * r;
-            s[j][r] = (col < m && row < n) ? Sg[(size_t)row * m + col] : 0.f;
+            s[j][r] = (col < m && row < n) ? osm[row * lds + col] : 0.f;
             ss = fmaf(s[j][r], s[j][r], ss);
         }
         nrm0[j] = sqrtf(warp_sum(ss));
     }
+    __syncthreads();                                  // osm is rewritten with Q~ below
     // one pass; the published column alternates between two buffers so that a
     // single barrier per column separates its writer from its readers
     for (int c = 0; c < m; ++c) {
@@ -1245,6 +1252,40 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
     // C = Q~^T Q~ (exact products of tf32 values, fp32 sums; the same
     // summation tree for C[a][c] and C[c][a], so C is exactly symmetric)
     float* Cq = sc.Cq + (size_t)item * m * m;
+    if (m <= 32) {
+        // each lane's partial dots with all m columns, then one butterfly
+        // reduce-scatter (lane c ends with column c; 31 shuffles).  Every
+        // element is summed over the same tree of lanes, so C stays symmetric.
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const int a = warp + kOrthWarps * j;
+            if (a >= m) continue;
+            float p[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) p[c] = 0.f;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int row = lane + 32 * r;
+                if (row < n) {
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        if (c < m) p[c] = fmaf(s[j][r], osm[row * lds + c], p[c]);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const bool up = (lane & off) != 0;
+#pragma unroll
+                for (int i = 0; i < off; ++i) {
+                    const float send = up ? p[i] : p[i + off];
+                    const float keep = up ? p[i + off] : p[i];
+                    p[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                }
+            }
+            if (lane < m) Cq[a * m + lane] = p[0];
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < CPW; ++j) {
         const int a = warp + kOrthWarps * j;
