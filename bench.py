@@ -217,18 +217,27 @@ def union_rows(ts, te):
     return total
 
 
+def kernel_text_sha256(path, begin, end):
+    """SHA-256 of a kernel's own source text: the slice of `path` from the
+    line holding `begin` up to (not including) the one holding `end`."""
+    import hashlib
+    with open(os.path.join(ROOT, path), encoding="utf-8") as fh:
+        text = fh.read()
+    a = text.index(begin)
+    b = text.index(end, a)
+    return hashlib.sha256(text[a:b].encode("utf-8")).hexdigest()
+
+
 def measured_traffic(name, units_per_launch):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     capture (profiles/lift_tc_traffic.json: bytes per output row, scaled by the
-    launch's output rows), or None when no capture covers this kernel or its
-    source has changed since the counters were taken."""
-    import hashlib
+    launch's output rows), or None when no capture covers this kernel or the
+    kernel's source text has changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "lift_tc_traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        with open(os.path.join(ROOT, rec["kernel_source"]), "rb") as fh:
-            cur = hashlib.sha256(fh.read()).hexdigest()
+        cur = kernel_text_sha256(rec["kernel_source"], rec["kernel_begin"], rec["kernel_end"])
     except (OSError, KeyError, ValueError):
         return None
     if rec.get("kernel") != name or rec.get("kernel_source_sha256") != cur:

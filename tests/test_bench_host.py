@@ -30,6 +30,17 @@ def test_lift_model_counts_writes_and_distinct_reads():
     assert bound == "hbm" and units == (1000 + 400) * w.k * 4
 
 
+def test_kernel_text_hash_covers_only_the_kernel(tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("head\n// BEGIN k\nbody 1\n// END\ntail\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h1 = bench.kernel_text_sha256("k.cuh", "// BEGIN k", "// END")
+    src.write_text("other head\n// BEGIN k\nbody 1\n// END\nother tail\n")
+    assert bench.kernel_text_sha256("k.cuh", "// BEGIN k", "// END") == h1
+    src.write_text("head\n// BEGIN k\nbody 2\n// END\ntail\n")
+    assert bench.kernel_text_sha256("k.cuh", "// BEGIN k", "// END") != h1
+
+
 def test_measured_traffic_only_for_the_captured_kernel():
     assert bench.measured_traffic("sketch", 1000) is None
     t1 = bench.measured_traffic("lift", 1000)
