@@ -193,6 +193,22 @@ zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out,
 zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
                          int32_t k_out, const zs_result* results, void* stream);
 
+/* Similar-range search (Section 6, case study).  L = base_te - base_ts + 1;
+ * the windows are the ranges [t, t + L - 1] with t = base_ts - j * stride
+ * >= 0, j = 1 .. nwin, nwin = min(max_windows, base_ts / stride).  Each is
+ * scored by the cosine <u_1, u_1^base> / (|u_1| |u_1^base|) of its first
+ * left singular vector (as zs_query gives it with k_out = 1, so with the
+ * same sign rule) with the base range's; a zero vector scores 0.  starts
+ * (host int64, >= max_windows entries) receives the window starts in that
+ * order, cos (host double, >= max_windows) their scores, *nwin (host) the
+ * count.  The windows run through zs_query_batch in chunks; the call
+ * allocates its scratch (the base's and one chunk's first vectors), works
+ * on `stream`, synchronises it and frees the scratch before it returns.
+ * ZS_ERANGE for a bad base range, ZS_EINVAL for stride < 1 or a null
+ * pointer, ZS_ENOMEM if the scratch cannot be allocated.                   */
+zs_status zs_similar_ranges(zs_store* st, int64_t base_ts, int64_t base_te, int64_t stride, int32_t max_windows,
+                            int64_t* starts, double* cos, int32_t* nwin, void* stream);
+
 /* Autotuner (no counterpart in the paper): times the query launch set on
  * nq deterministic ranges of the store's current rows under candidate grid
  * shapes (persistent CTAs per SM of the slab work-list and projection

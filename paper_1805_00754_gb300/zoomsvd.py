@@ -60,6 +60,9 @@ SIGNATURES = {
     "zs_store_reset": (C.c_int, [C.c_void_p]),
     "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "zs_store_fault": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "zs_similar_ranges": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32),
+                                    C.c_void_p]),
     "zs_store_export_block": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
     "zs_compress_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int64, C.c_int64,
@@ -214,6 +217,21 @@ class Store:
         r = out.as_c()
         _check(lib().zs_query(self._h, ts, te, k_out, C.byref(r), _stream_ptr(stream)))
         return out
+
+    def similar_ranges(self, base, stride: int, max_windows: int | None = None, stream=None):
+        """Windows of the base range's length starting stride, 2 stride, ...
+        rows before it, scored by the cosine of their first left singular
+        vector with the base's (Section 6): [(start, cosine), ...]."""
+        t_s, t_e = int(base[0]), int(base[1])
+        cap = max(0, t_s // max(int(stride), 1)) if max_windows is None else int(max_windows)
+        starts = np.zeros(max(cap, 1), dtype=np.int64)
+        cos = np.zeros(max(cap, 1), dtype=np.float64)
+        nw = C.c_int32()
+        _check(lib().zs_similar_ranges(self._h, t_s, t_e, int(stride), cap,
+                                       starts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       cos.ctypes.data_as(C.POINTER(C.c_double)), C.byref(nw),
+                                       _stream_ptr(stream)))
+        return [(int(starts[j]), float(cos[j])) for j in range(nw.value)]
 
     def query_batch(self, ts, te, k_out: int | None = None, outs=None, stream=None):
         k_out = self.k if k_out is None else k_out
