@@ -421,6 +421,69 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+SWEEP_B = (64, 128, 256, 512, 1_024, 2_048, 4_096, 8_192, 16_384, 65_536)
+SWEEP_LEN = (1_000, 10_000, 100_000)
+
+
+def sweep_batch_size(L, b, k, n, itemsize=4, cap=256, budget=2 << 30):
+    """Queries per timed batch of length-L ranges: at most `cap`, and few
+    enough that the stacked matrices ((L / b + 2) slabs of k x n each per
+    query) stay within `budget` bytes."""
+    per_query = (L // b + 2) * k * n * itemsize
+    return int(max(1, min(cap, budget // per_query)))
+
+
+def run_sweep_b(args, w):
+    """Block-size sweep (the trade-off of Fig. 7 on the synthetic workload).
+    For each b: the time to compress the whole matrix (CUDA events, inputs in
+    HBM), the bytes the store keeps (Theorem 3) and queries/s for batches of
+    fixed-length ranges L = 1e3, 1e4, 1e5 (U materialised).  One JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_00754_gb300 as zs
+
+    T, n, k = w.series.T, w.series.n, w.k
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    rows_dev = torch.from_numpy(_input_rows(w)).cuda()
+    stream = torch.cuda.current_stream()
+    points = []
+    for b in SWEEP_B:
+        st = zs.Store(n=n, b=b, k=k, dtype=w.dtype, capacity_rows=T)
+        st.append(rows_dev)                      # warm-up (allocations, first launches)
+        torch.cuda.synchronize()
+        st.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.append(rows_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        comp_ms = e0.elapsed_time(e1)
+        _, nblk, fbytes = st.info()
+        qps = {}
+        for L in SWEEP_LEN:
+            nq = sweep_batch_size(L, b, k, n)
+            ts, te = synthetic.queries(T, nq, L, L, seed=synthetic.SEED_BASE + 7 + L)
+            outs = [st.new_result(int(a), int(z), k) for a, z in zip(ts, te)]
+            st.query_batch(ts, te, k, outs)      # warm-up
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                st.query_batch(ts, te, k, outs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            qps[str(L)] = 3 * nq / (e0.elapsed_time(e1) / 1e3)
+            del outs
+        assert st.fault() == 0
+        points.append({"b": b, "blocks": nblk, "compress_ms": comp_ms,
+                       "compress_gbs": T * n * itemsize / comp_ms / 1e6, "factor_bytes": fbytes,
+                       "space_vs_raw": fbytes / (T * n * itemsize), "queries_per_s": qps})
+        st.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "block_size", "workload": w.name, "T": T, "n": n, "k": k,
+                      "dtype": w.dtype, "lengths": list(SWEEP_LEN), "points": points}))
+
+
 def plain_fp64_run(w, A, ts, te, local, budget_s=4.0, acc_queries=3):
     """The same range-SVD method as a plain FP64 GPU program, one query at a
     time: an FP64 store of the same rows (FP64 CUDA-core kernels throughout),
@@ -593,10 +656,14 @@ def main():
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="skip the one-query-at-a-time FP64 GPU form")
     ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")
+    ap.add_argument("--sweep-b", action="store_true",
+                    help="block-size sweep (compression time, space, queries/s at 1e3/1e4/1e5 rows)")
     args = ap.parse_args()
     w = synthetic.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.sweep_b:
+        run_sweep_b(args, w)
     else:
         run_gpu(args, w)
 

@@ -46,3 +46,13 @@ def test_measured_traffic_only_for_the_captured_kernel():
     t1 = bench.measured_traffic("lift", 1000)
     if t1 is not None:               # the capture matches the current kernel source
         assert abs(bench.measured_traffic("lift", 2000) - 2 * t1) < 1e-6 * t1
+
+
+def test_sweep_batch_size_bounds_the_stacked_bytes():
+    budget = 2 << 30
+    for b in bench.SWEEP_B:
+        for L in bench.SWEEP_LEN:
+            nq = bench.sweep_batch_size(L, b, 16, 256, budget=budget)
+            assert 1 <= nq <= 256
+            assert nq == 1 or nq * (L // b + 2) * 16 * 256 * 4 <= budget
+    assert bench.sweep_batch_size(100_000, 64, 16, 256) < 256
