@@ -129,6 +129,16 @@ zs_status zs_store_reset(zs_store* st);
 zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
                         int64_t* factor_bytes);
 
+/* Energy rule (Eq. 1) for the blocks compressed from now on: xi in (0, 1]
+ * gives block i the rank k_i = the smallest rank whose leading singular
+ * values hold a fraction >= xi of ||X_i||_F^2 (the sum of all the block's
+ * sigma_j^2), capped at the store's k; columns k_i.. of its U, sigma and V
+ * are stored as zeros (the arrays keep width k), which queries treat as rank
+ * deficiency.  xi = 0 restores the fixed rank k.  Costs one more read of each
+ * block's rows per append.  ZS_EINVAL for xi outside [0, 1], ZS_ENOMEM if the
+ * per-block scratch (8 bytes per block of capacity) cannot be allocated.    */
+zs_status zs_store_set_xi(zs_store* st, double xi);
+
 /* Device fault word of the store (failure detection): 1 once a kernel of
  * this store gave up a bounded wait on the device (the tensor-core
  * projection waits on its MMA completions with an iteration limit, then

@@ -175,12 +175,30 @@ def compress_block_incremental(Ab: np.ndarray, k: int):
     return truncate(U, s, Vt, k)
 
 
-def compress(A: np.ndarray, b: int, k: int, incremental: bool = False) -> Store:
-    """Storage phase (Algorithm 1): compress every block of A (T x n)."""
+def compress_block_xi(Ab: np.ndarray, k: int, xi: float):
+    """Stored factors of one block under the energy rule (Eq. 1): rank
+    k_i = min(k, smallest rank holding a fraction >= xi of the block's
+    energy), kept in arrays of width k with columns k_i.. zero."""
+    U, s, Vt = compress_block(Ab, k)
+    ki = min(U.shape[1], rank_xi(svd(Ab)[1], xi))
+    U, s, Vt = U.copy(), s.copy(), Vt.copy()
+    U[:, ki:] = 0.0
+    s[ki:] = 0.0
+    Vt[ki:, :] = 0.0
+    return U, s, Vt
+
+
+def compress(A: np.ndarray, b: int, k: int, incremental: bool = False, xi: float | None = None) -> Store:
+    """Storage phase (Algorithm 1): compress every block of A (T x n); with
+    xi, each block keeps the rank Eq. 1 gives it (at most k)."""
     A = np.asarray(A, dtype=np.float64)
     T, n = A.shape
     st = Store(b=b, n=n, k=k, T=T, U=[], s=[], Vt=[])
-    f = compress_block_incremental if incremental else compress_block
+    if xi is not None:
+        def f(Ab, kk):
+            return compress_block_xi(Ab, kk, xi)
+    else:
+        f = compress_block_incremental if incremental else compress_block
     for lo, hi in block_bounds(T, b):
         U, s, Vt = f(A[lo:hi], k)
         st.U.append(U)

@@ -442,6 +442,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     auto f = [](void*& p) { if (p) cudaFree(p); p = nullptr; };
     f(st->U); f(st->sig); f(st->vt); f(st->w); if (st->d_fault) cudaFree(st->d_fault); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
     f(st->qb); f(st->ys); f(st->aux);
+    if (st->d_energy) cudaFree(st->d_energy);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
@@ -500,6 +501,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
             ch.vt = st->vt;
             ch.w = st->w;
             ch.fault = st->d_fault;
+            ch.xi = st->xi;
+            ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
             ch.ews = st->ews;
             ch.ews_ctas = st->ews_ctas;
             ch.qb = (char*)st->qb + (size_t)r * sub * 4 * tc_qb_floats((int)m, (int)c.n);
@@ -534,6 +537,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.vt = st->vt;
         ch.w = st->w;
         ch.fault = st->d_fault;
+        ch.xi = st->xi;
+        ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
         ch.ews = st->ews;
         ch.ews_ctas = st->ews_ctas;
         ch.qb = st->qb;
@@ -695,6 +700,23 @@ extern "C" zs_status zs_store_reset(zs_store* st) {
     }
     st->pending.clear();
     st->T = 0;
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_set_xi(zs_store* st, double xi) {
+    if (!st) return fail(ZS_EINVAL, "null store");
+    if (!(xi >= 0.0 && xi <= 1.0)) return fail(ZS_EINVAL, "xi %g not in [0, 1]", xi);
+    std::lock_guard<std::mutex> lk(st->mu);
+    DeviceGuard g(st->cfg.device);
+    if (xi > 0.0 && !st->d_energy) {
+        const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(st->cap_blocks, 1);
+        if (cudaMalloc((void**)&st->d_energy, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            st->d_energy = nullptr;
+            return fail(ZS_ENOMEM, "block energies (%zu bytes)", bytes);
+        }
+    }
+    st->xi = xi;
     return ZS_OK;
 }
 

@@ -65,6 +65,8 @@ struct zs_store {
     void* vt = nullptr;            // cap_blocks x k x n
     void* w = nullptr;             // tensor path: cap_blocks x k x n, Sigma V^T (the stack-ready slabs)
     int* d_fault = nullptr;        // device fault word (bounded waits that gave up)
+    double xi = 0.0;               // > 0: energy rule (Eq. 1) picks each block's rank <= k
+    double* d_energy = nullptr;    // xi > 0: per slot ||X_i||_F^2 (cap_blocks doubles)
     void* tail = nullptr;          // b x n raw rows of the open block
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace

@@ -41,6 +41,8 @@ struct CompressChunk {
     void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
     void* aux;        // tensor path: tc_aux_bytes(nblk, nblk*ceil(b/128), m, k)
     int* fault;       // device word set to 1 when a bounded wait gives up (or null)
+    double xi;        // > 0: energy rule of Eq. 1 per block (rank k_i <= k), else fixed k
+    double* energy;   // xi > 0: nblk doubles of scratch (each block's squared Frobenius norm)
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).

@@ -2,12 +2,14 @@
 // (CUDA events on the launch stream), the launch counter, the eigen-core and
 // tensor-path scratch plans, and the dispatch of the storage- and query-phase
 // launch sets to their per-precision translation units.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "zs_internal.h"
@@ -154,10 +156,100 @@ cudaError_t launch_query_f32(const QueryArgs& a, const QueryGrid& g, int flags, 
 cudaError_t launch_query_f32_refine(const QueryArgs& a, const QueryGrid& g, int flags, const Tuning& tu,
                                     int num_sms, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Energy rule (Eq. 1) per block: k_i = the smallest rank whose leading
+// singular values hold a fraction >= xi of the block's energy ||X_i||_F^2
+// (the sum of all its sigma_j^2), capped at the stored k.  Applied after the
+// block's rank-k factors are formed: columns k_i.. of U, sigma, V^T (and the
+// stored Sigma V^T) become zero, which the query phase treats as rank
+// deficiency.
+// ---------------------------------------------------------------------------
+// ||X_i||_F^2 of each block of the chunk, FP64 sums in a fixed order
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_block_energy(CompressChunk c) {
+    __shared__ double red[8];
+    const int j = blockIdx.x;
+    if (j >= c.nblk) return;
+    const int rows = (int)min((int64_t)c.b, c.rows_total - (int64_t)j * c.b);
+    const Tin* X = (const Tin*)c.A + (size_t)j * c.b * c.lda;
+    double e = 0.0;
+    for (int64_t f = threadIdx.x; f < (int64_t)rows * c.n; f += 256) {
+        const int64_t r = f / c.n, col = f - (f / c.n) * c.n;
+        double x;
+        if constexpr (std::is_same<Tin, __nv_bfloat16>::value) x = (double)__bfloat162float(X[r * c.lda + col]);
+        else x = (double)X[r * c.lda + col];
+        e = fma(x, x, e);
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        c.energy[j] = s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_xi_truncate(CompressChunk c) {
+    __shared__ int ki_s;
+    const int j = blockIdx.x;
+    if (j >= c.nblk) return;
+    const int64_t slot = (int64_t)c.slot0 + j;
+    const int k = c.k, n = c.n;
+    T* sig = (T*)c.sig + slot * k;
+    if (threadIdx.x == 0) {
+        const double e = c.energy[j], goal = c.xi * e;
+        int ki = 0;
+        if (e > 0.0) {
+            ki = k;
+            double cum = 0.0;
+            for (int l = 0; l < k; ++l) {
+                cum += (double)sig[l] * (double)sig[l];
+                if (cum >= goal) {
+                    ki = l + 1;
+                    break;
+                }
+            }
+        }
+        ki_s = ki;
+    }
+    __syncthreads();
+    const int ki = ki_s;
+    if (ki >= k) return;
+    const int rows = (int)min((int64_t)c.b, c.rows_total - (int64_t)j * c.b);
+    T* U = (T*)c.U + slot * c.b * k;
+    T* Vt = (T*)c.vt + slot * k * n;
+    T* W = c.w ? (T*)c.w + slot * k * n : nullptr;
+    const int dk = k - ki;
+    for (int l = threadIdx.x; l < dk; l += 256) sig[ki + l] = T(0);
+    for (int64_t f = threadIdx.x; f < (int64_t)rows * dk; f += 256) {
+        const int64_t r = f / dk;
+        U[r * k + ki + (f - r * dk)] = T(0);
+    }
+    for (int64_t f = threadIdx.x; f < (int64_t)dk * n; f += 256) {
+        Vt[(int64_t)ki * n + f] = T(0);
+        if (W) W[(int64_t)ki * n + f] = T(0);
+    }
+}
+
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
                             cudaStream_t st) {
-    if (use_tc_path(fp64, c.n, flags)) return launch_compress_tc(c, flags, tu, num_sms, st);
-    return launch_compress_simt(c, fp64, flags, tu, num_sms, st);
+    cudaError_t e = use_tc_path(fp64, c.n, flags) ? launch_compress_tc(c, flags, tu, num_sms, st)
+                                                   : launch_compress_simt(c, fp64, flags, tu, num_sms, st);
+    if (e != cudaSuccess || !(c.xi > 0.0) || !c.energy || c.nblk < 1) return e;
+    {
+        prof::Scope ps("xi_energy", st);
+        if (c.in_kind == IN_F64) k_block_energy<double><<<c.nblk, 256, 0, st>>>(c);
+        else if (c.in_kind == IN_BF16) k_block_energy<__nv_bfloat16><<<c.nblk, 256, 0, st>>>(c);
+        else k_block_energy<float><<<c.nblk, 256, 0, st>>>(c);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    prof::Scope ps("xi_truncate", st);
+    if (fp64) k_xi_truncate<double><<<c.nblk, 256, 0, st>>>(c);
+    else k_xi_truncate<float><<<c.nblk, 256, 0, st>>>(c);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_query(const QueryArgs& a, bool fp64, const QueryGrid& g, int flags, const Tuning& tu,

@@ -60,6 +60,7 @@ SIGNATURES = {
     "zs_store_reset": (C.c_int, [C.c_void_p]),
     "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "zs_store_fault": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "zs_store_set_xi": (C.c_int, [C.c_void_p, C.c_double]),
     "zs_similar_ranges": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                     C.c_void_p]),
@@ -141,7 +142,7 @@ class Store:
     """A compressed range-SVD store on one GPU (the sets U, S, V of Def. 2)."""
 
     def __init__(self, n: int, b: int, k: int, dtype: str = "f32", capacity_rows: int = 1 << 20,
-                 device: int = 0, fp64_refine: bool = False, exact_gram: bool = False):
+                 device: int = 0, fp64_refine: bool = False, exact_gram: bool = False, xi: float | None = None):
         self.n, self.b, self.k, self.dtype = n, b, k, dtype
         self.device = torch.device("cuda", device)
         self.fdtype = factor_dtype(dtype)
@@ -150,6 +151,12 @@ class Store:
         h = C.c_void_p()
         _check(lib().zs_store_create(C.byref(cfg), C.byref(h)))
         self._h = h
+        if xi is not None:
+            self.set_xi(xi)
+
+    def set_xi(self, xi: float):
+        """Energy rule (Eq. 1) for blocks compressed from now on; 0 = fixed k."""
+        _check(lib().zs_store_set_xi(self._h, float(xi)))
 
     def close(self):
         if getattr(self, "_h", None):

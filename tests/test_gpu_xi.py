@@ -1,0 +1,98 @@
+"""GPU parity of the energy rule (Eq. 1, zs_store_set_xi): per-block ranks,
+stored factors and queries against the oracle's compress(..., xi=...).
+
+The xi values are chosen so that every block's decision sits at least 1e-4
+(FP64) or 2e-3 (FP32) away from the threshold in the oracle's energy ratios,
+far above each path's error in sigma, and so that the ranks differ between
+blocks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from tests._parity import compare_query, device_rows, _to_np
+
+pytestmark = pytest.mark.gpu
+
+F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-10)
+F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=5e-4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _xi_store(A64, b, k, dtype, xi):
+    from paper_1805_00754_gb300 import Store
+    rows, exact = device_rows(A64, dtype)
+    st = Store(n=A64.shape[1], b=b, k=k, dtype=dtype, capacity_rows=A64.shape[0], xi=xi)
+    st.append(rows)
+    torch.cuda.synchronize()
+    return st, exact
+
+
+def _check_blocks(st, ost, rtol):
+    ranks = []
+    for i in range(len(ost.s)):
+        U, s, Vt, ki = st.export_block(i)
+        s = _to_np(s)
+        ref = np.zeros_like(s)
+        ref[:ost.s[i].shape[0]] = ost.s[i]
+        r_gpu, r_ref = int(np.count_nonzero(s)), int(np.count_nonzero(ref))
+        assert r_gpu == r_ref, f"block {i}: rank {r_gpu} != {r_ref}"
+        np.testing.assert_allclose(s[:r_ref], ref[:r_ref], rtol=rtol)
+        assert np.all(_to_np(U)[:, r_ref:] == 0) and np.all(_to_np(Vt)[r_ref:] == 0)
+        ranks.append(r_ref)
+    return ranks
+
+
+def test_xi_f64_plain_workload():
+    w = synthetic.WORKLOADS["plain_f64"]
+    A = synthetic.rows(w.series)
+    st, exact = _xi_store(A, w.b, w.k, "f64", 0.9)
+    ost = oracle.compress(exact, w.b, w.k, xi=0.9)
+    ranks = _check_blocks(st, ost, 1e-10)
+    assert len(set(ranks)) > 1 and max(ranks) < w.k
+    for a, z in [(1_234, 15_678), (0, 19_999), (499, 500), (7_000, 7_400)]:
+        # the range's rank r can be below k here (a range inside one block has
+        # that block's k_i); its r pairs meet the oracle, and the directions
+        # past r, exactly zero in the oracle, come back through the Gram route
+        # at most ~sqrt(eps) sigma_1
+        full = oracle.query(ost, a, z, k_out=w.k)
+        r = int(np.count_nonzero(full.s))
+        out = st.query(a, z, k_out=r)
+        torch.cuda.synchronize()
+        compare_query(out, oracle.query(ost, a, z, k_out=r), **F64, label=f"xi f64 [{a},{z}]")
+        res = st.query(a, z, k_out=w.k)
+        torch.cuda.synchronize()
+        tail = _to_np(res.S)
+        assert np.all(tail[r:] <= 1e-6 * tail[0]), f"[{a},{z}] tail {tail[r:]}"
+
+
+def test_xi_f32_tensor_path_ragged():
+    w = synthetic.WORKLOADS["ragged_batch_f32"]
+    A = synthetic.rows(w.series, 0, 8 * w.b + 304)
+    st, exact = _xi_store(A, w.b, w.k, "f32", 0.8)
+    ost = oracle.compress(exact, w.b, w.k, xi=0.8)
+    ranks = _check_blocks(st, ost, 1e-4)
+    assert len(set(ranks)) > 1
+    T = A.shape[0]
+    for a, z in [(0, T - 1), (1_999, 2_000), (3_333, 12_345), (15_000, T - 1)]:
+        out = st.query(a, z)
+        torch.cuda.synchronize()
+        compare_query(out, oracle.query(ost, a, z), **F32, label=f"xi f32 [{a},{z}]")
+    assert st.fault() == 0
+
+
+def test_xi_errors_and_reset_to_fixed():
+    from paper_1805_00754_gb300 import Store, ZsError
+    st = Store(n=16, b=64, k=4, dtype="f32", capacity_rows=256)
+    with pytest.raises(ZsError) as e:
+        st.set_xi(1.5)
+    assert e.value.status == 1
+    st.set_xi(0.0)                       # fixed rank again

@@ -261,6 +261,41 @@ def test_tiny_bruteforce_every_range(b):
         _same_result(r2, oracle.direct_svd(oracle.reconstruct(trunc, ts, te), 2), 1e-10, 1e-7)
 
 
+@pytest.mark.parametrize("xi", [0.5, 0.9, 0.99])
+def test_xi_compress_energy_rule(xi):
+    """Eq. 1 per block, checked against the data: the kept rank k_i holds at
+    least xi of ||X_i||_F^2 (unless capped at k), one rank less does not, and
+    the stored block's residual is the Eckart-Young tail."""
+    g = np.random.default_rng(5)
+    A = g.standard_normal((300, 6)) @ np.diag([5.0, 3.0, 2.0, 1.0, 0.5, 0.1])
+    b, k = 64, 4
+    st = oracle.compress(A, b, k, xi=xi)
+    ranks = []
+    for i, (lo, hi) in enumerate(oracle.block_bounds(300, b)):
+        X = A[lo:hi]
+        E = float(np.sum(X ** 2))
+        s = st.s[i]
+        ki = int(np.count_nonzero(s))
+        ranks.append(ki)
+        kept = float(np.sum(s[:ki] ** 2))
+        if ki < k:
+            assert kept >= xi * E * (1 - 1e-12)
+        if ki >= 1:
+            assert float(np.sum(s[:ki - 1] ** 2)) < xi * E
+        R = X - st.U[i] @ np.diag(s) @ st.Vt[i]
+        assert float(np.sum(R ** 2)) == pytest.approx(E - kept, rel=1e-9, abs=1e-9 * E)
+    assert min(ranks) >= 1 and max(ranks) <= k
+
+
+def test_xi_one_is_fixed_rank():
+    g = np.random.default_rng(6)
+    A = g.standard_normal((200, 5))
+    a, z = oracle.compress(A, 50, 3), oracle.compress(A, 50, 3, xi=1.0)
+    for i in range(len(a.s)):
+        np.testing.assert_array_equal(a.s[i], z.s[i])
+        np.testing.assert_array_equal(a.U[i], z.U[i])
+
+
 def test_similar_range_search_periodic():
     """Section 6: a window shifted by whole periods of a periodic signal matches."""
     t = np.arange(1200)
