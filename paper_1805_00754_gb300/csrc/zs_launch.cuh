@@ -230,11 +230,17 @@ static void lift_launch(const QueryArgs& a, int64_t max_slabs, int num_sms, cuda
         // tensor-core lift: per warp two split copies of C in shared memory
         const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;
         const int wpc = threads / 32;
-        const size_t sm = sizeof(float) * lift_tc_warp_floats<KMAX, QMAX>() * wpc;
-        set_smem(k_lift_tc<KMAX, QMAX>, sm);
         const int grid =
             (int)std::max<int64_t>(1, std::min<int64_t>((max_slabs + wpc - 1) / wpc, (int64_t)num_sms * 8));
-        k_lift_tc<KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+        if (a.k % 16 == 0) {
+            const size_t sm = sizeof(float) * lift_tc_warp_floats<KMAX, QMAX>() * wpc;
+            set_smem(k_lift_tc<KMAX, QMAX>, sm);
+            k_lift_tc<KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+        } else {
+            const size_t sm = sizeof(float) * lift_nat_warp_floats<KMAX, QMAX>() * wpc;
+            set_smem(k_lift_tc_nat<KMAX, QMAX>, sm);
+            k_lift_tc_nat<KMAX, QMAX><<<grid, threads, sm, st>>>(a);
+        }
     } else {
         const int threads = (KMAX * QMAX >= 2048) ? 128 : 256;       // register budget
         const int wpc = threads / 32;

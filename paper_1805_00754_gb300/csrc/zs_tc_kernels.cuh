@@ -1905,6 +1905,129 @@ __global__ void __launch_bounds__(256) k_lift_tc(QueryArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// 5'. Lift for k not a multiple of 16 (the K order of k_lift_tc would waste a
+//    step on a partly filled 16-column group): the same product in natural K
+//    order: the stored U_i rows times each slab's coefficients C (k x kq)
+//    (Algorithm 2, last step; Eq. 9), one warp per slab, 16 rows per step, U
+//    fragments of the next step loaded before the current step's products.
+//    U rows and C are split into two tf32 terms each (three products); C is
+//    split once per slab into two shared tiles.
+// ---------------------------------------------------------------------------
+template <int QMAX>
+__host__ __device__ constexpr int lift_ldc_nat() { return (QMAX + 31) / 32 * 32 + 8; }
+template <int KMAX, int QMAX>
+__host__ __device__ __forceinline__ size_t lift_nat_warp_floats() { return (size_t)2 * KMAX * lift_ldc_nat<QMAX>(); }
+
+template <int KMAX, int QMAX>
+__global__ void __launch_bounds__(256) k_lift_tc_nat(QueryArgs a) {
+    extern __shared__ __align__(16) float lsm[];
+    constexpr int LDC = lift_ldc_nat<QMAX>();
+    const int k = a.k, kq = a.kq, kout = a.kout;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    float* Ch = lsm + (size_t)warp * lift_nat_warp_floats<KMAX, QMAX>();
+    float* Cl = Ch + KMAX * LDC;
+    const int nq = a.hdr->nq;
+    const int64_t total = a.hdr->nslab_total, Trows = a.hdr->T;
+    const int nkt = (k + 7) / 8, nnt = (kout + 7) / 8;
+    // each warp takes a contiguous range of slabs, so the owning query only
+    // advances (one search per warp instead of one per slab)
+    const int64_t nw = (int64_t)gridDim.x * wpc, wid = (int64_t)blockIdx.x * wpc + warp;
+    const int64_t per = (total + nw - 1) / nw;
+    const int64_t s_lo = wid * per, s_hi = min(total, s_lo + per);
+    int q = s_lo < s_hi ? find_query(a.slab_prefix, nq, s_lo) : 0;
+    for (int64_t s = s_lo; s < s_hi; ++s) {
+        while (q + 1 < nq && a.slab_prefix[q + 1] <= s) ++q;
+        const QPlan& P = a.plans[q];
+        const int t = (int)(s - P.slab0);
+        const BlockRange br = slab_rows(P, t, a.b, Trows);
+        const float* U = (const float*)a.U + (int64_t)br.blk * a.b * k;
+        const float* Cg = (const float*)a.C + s * k * kq;
+        __syncwarp();
+        for (int e = lane; e < KMAX * QMAX; e += 32) {
+            const int aa = e / QMAX, c = e % QMAX;
+            const float v = (aa < k && c < kq) ? Cg[aa * kq + c] : 0.f;
+            uint32_t h, l;
+            tf32_split(v, h, l);
+            Ch[aa * LDC + c] = __uint_as_float(h);
+            Cl[aa * LDC + c] = __uint_as_float(l);
+        }
+        __syncwarp();
+        float* out = (float*)P.U;
+        const int64_t o0 = (int64_t)br.blk * a.b - P.ts;
+        const bool pair = (kout % 2 == 0) && (P.ldu % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 7) == 0);
+        // U fragments of the next 16-row step are loaded before the current
+        // step's products (software pipeline over the slab's rows)
+        float nx[KMAX / 8][4];
+        auto fetch = [&](int r0, float (&dst)[KMAX / 8][4]) {
+            const int ra = r0 + g, rb = r0 + g + 8;
+            const bool va = ra < br.hi, vb = rb < br.hi;
+            const float* pa = U + (int64_t)ra * k;
+            const float* pb = U + (int64_t)rb * k;
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt) {
+                const int c0 = kt * 8 + t4, c1 = c0 + 4;
+                dst[kt][0] = (kt < nkt && va && c0 < k) ? __ldg(pa + c0) : 0.f;
+                dst[kt][1] = (kt < nkt && vb && c0 < k) ? __ldg(pb + c0) : 0.f;
+                dst[kt][2] = (kt < nkt && va && c1 < k) ? __ldg(pa + c1) : 0.f;
+                dst[kt][3] = (kt < nkt && vb && c1 < k) ? __ldg(pb + c1) : 0.f;
+            }
+        };
+        if (br.lo < br.hi) fetch(br.lo, nx);
+        for (int r0 = br.lo; r0 < br.hi; r0 += 16) {
+            float cx[KMAX / 8][4];
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cx[kt][e] = nx[kt][e];
+            if (r0 + 16 < br.hi) fetch(r0 + 16, nx);
+            float acc[QMAX / 8][4];
+#pragma unroll
+            for (int x = 0; x < QMAX / 8; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+            const int ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+            for (int kt = 0; kt < KMAX / 8; ++kt) {
+                if (kt >= nkt) break;
+                const int c0 = kt * 8 + t4;
+                uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+                tf32_split_trunc(cx[kt][0], h0, l0);
+                tf32_split_trunc(cx[kt][1], h1, l1);
+                tf32_split_trunc(cx[kt][2], h2, l2);
+                tf32_split_trunc(cx[kt][3], h3, l3);
+                const float* bh = Ch + c0 * LDC + g;
+                const float* bl = Cl + c0 * LDC + g;
+#pragma unroll
+                for (int nt = 0; nt < QMAX / 8; ++nt) {
+                    if (nt >= nnt) break;
+                    const uint32_t bh0 = __float_as_uint(bh[nt * 8]), bh1 = __float_as_uint(bh[4 * LDC + nt * 8]);
+                    const uint32_t bl0 = __float_as_uint(bl[nt * 8]), bl1 = __float_as_uint(bl[4 * LDC + nt * 8]);
+                    mma_tf32(acc[nt], l0, l1, l2, l3, bh0, bh1);
+                    mma_tf32(acc[nt], h0, h1, h2, h3, bl0, bl1);
+                    mma_tf32(acc[nt], h0, h1, h2, h3, bh0, bh1);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < QMAX / 8; ++nt) {
+                if (nt >= nnt) break;
+                const int c = nt * 8 + 2 * t4;
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int r = hh ? rb : ra;
+                    if (r >= br.hi || c >= kout) continue;
+                    float* orow = out + (o0 + r) * P.ldu + c;
+                    if (pair) {
+                        *reinterpret_cast<float2*>(orow) = make_float2(acc[nt][2 * hh], acc[nt][2 * hh + 1]);
+                    } else {
+                        orow[0] = acc[nt][2 * hh];
+                        if (c + 1 < kout) orow[1] = acc[nt][2 * hh + 1];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Partial-SVD (Algorithm 3; Eq. 5-6) of one boundary slab per warp, float
 // stores with k <= KB <= 32:
 //   H = Sigma (X U)^T (X U) Sigma over the slab's rows on tf32 tensor cores
