@@ -51,6 +51,21 @@ def test_store_create_rejects_bad_config_without_gpu():
     assert lib.zs_store_create(ctypes.byref(cfg), ctypes.byref(h)) == 6
 
 
+def test_new_entry_points_reject_bad_arguments_without_gpu():
+    """zs_similar_ranges and zs_store_set_xi check their arguments before any
+    device call."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1805_00754_gb300 import zoomsvd
+    lib = zoomsvd.load_library()
+    starts = (ctypes.c_int64 * 4)()
+    cos = (ctypes.c_double * 4)()
+    nw = ctypes.c_int32()
+    assert lib.zs_similar_ranges(None, 10, 20, 5, 4, starts, cos, ctypes.byref(nw), None) == 1
+    assert lib.zs_store_set_xi(None, 0.9) == 1
+    assert b"null" in lib.zs_last_error()
+
+
 def test_generators_deterministic_and_chunk_independent():
     spec = synthetic.SeriesSpec(20_000, 8, 3, 0.05, 1e-3, 7)
     full = synthetic.rows(spec)
