@@ -932,7 +932,6 @@ __global__ void __cluster_dims__(kSketchCL, 1, 1) __launch_bounds__(256, (NMT * 
     __nv_bfloat16* Xs = (__nv_bfloat16*)dsm;
     float* Sp = (float*)dsm;                          // npad x lds (after the tiles)
     const int chunk = (npad + kSketchCL - 1) / kSketchCL;
-    float* Ssl = Sp + (size_t)npad * lds;              // chunk x lds
     __nv_bfloat16* Bs = (__nv_bfloat16*)(dsm + L.rx);
     __nv_bfloat16* Ws = (__nv_bfloat16*)(dsm + L.rx + L.bs);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1337,7 +1336,6 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
     char* rot = (char*)(X + (REF ? 2 * (size_t)m * ld : 0));
     rot = (char*)(((uintptr_t)rot + 15) & ~(uintptr_t)15);
     WarpRot<float>& wrf = *reinterpret_cast<WarpRot<float>*>(rot);
-    WarpRot<double>& wrd = *reinterpret_cast<WarpRot<double>*>(rot + ((sizeof(WarpRot<float>) + 15) & ~size_t(15)));
     const int count = src.count();
     for (int item = blockIdx.x * wpc + warp; item < count; item += gridDim.x * wpc) {
         const int rows = src.rows(item);
