@@ -46,7 +46,10 @@ typedef enum {
     ZS_EDTYPE = 6,      /* unsupported dtype combination                    */
     ZS_ECUDA = 7,       /* a CUDA runtime call failed                       */
     ZS_EINTERNAL = 8,   /* invariant violated inside the library            */
-    ZS_ENOTFOUND = 9    /* unknown ticket / block index                     */
+    ZS_ENOTFOUND = 9,   /* unknown ticket / block index                     */
+    ZS_ENOCONV = 10     /* a truncated SVD did not pass its accuracy test
+                           within the iteration cap (results are the last
+                           iterate; see zs_store_status)                    */
 } zs_status;
 
 typedef enum { ZS_F64 = 0, ZS_F32 = 1, ZS_BF16 = 2 } zs_dtype;
@@ -147,6 +150,26 @@ zs_status zs_store_set_xi(zs_store* st, double xi);
  * the word; a non-zero word persists until the store is destroyed.        */
 zs_status zs_store_fault(const zs_store* st, int32_t* flag);
 
+/* Accuracy status of the store (Section 2.1: each stored block is the
+ * rank-k truncated SVD of its rows; Algorithm 2: each answer the truncated
+ * SVD of the stacked matrix).  On float stores every block and every
+ * query's Stitched-SVD is tested on the device after it is computed: with
+ * R = X^T U from the factors as written, rho_j = |X^T u_j - sigma_j v_j|
+ * and the bound beta_j = min(rho_j, rho_j^2 / (sigma_j - s_m)) on the
+ * error of sigma_j (s_m the smallest Ritz value of the subspace), an item
+ * passes when beta_j <= 1e-5 sigma_j for every kept pair.  Items that fail
+ * are refined by subspace iteration (64 directions, at most 12 passes over
+ * their rows); one that still fails keeps its last iterate and is counted
+ * here.  Synchronises the device.  *unconverged_blocks and
+ * *unconverged_queries (host, may be NULL) receive the counts since the
+ * store was created, *refined_blocks and *refined_queries (may be NULL)
+ * how many items needed refinement at all.  Returns ZS_ENOCONV if an
+ * unconverged count is nonzero, ZS_ETIMEDOUT if the fault word of
+ * zs_store_fault is set, else ZS_OK.  FP64 stores use an exact Gram
+ * eigen-solver and never count here.                                       */
+zs_status zs_store_status(const zs_store* st, int64_t* unconverged_blocks, int64_t* unconverged_queries,
+                          int64_t* refined_blocks, int64_t* refined_queries);
+
 /* Copy block i's stored factors into caller device buffers: U (rows_i x k,
  * ld k), sigma (k), Vt (k x n, ld n), on `stream`.  *rows_i and *k_i (host)
  * receive the block's row count and kept rank min(k, rows_i, n); columns
@@ -165,20 +188,34 @@ zs_status zs_store_export_block(const zs_store* st, int64_t i, void* U, void* si
  * zero), sigma + j*k (k) and Vt + j*k*n (k x n, ld n), in the factor type
  * (double for ZS_F64 input, else float).  flags takes ZS_FLAG_FP64_REFINE.
  * Its scratch is one fixed 32 MiB device array inside the library (held on
- * every device that loads the library until the process exits): the
- * per-block n x n Gram matrices of a chunk of blocks plus, for large n, the
- * eigen core's workspace.  n whose per-block scratch does not fit is
- * rejected with ZS_EINVAL; the call makes no cudaMalloc, cudaFree or other
- * allocating call.  Every call uses the same array and overwrites the parts
- * it reads before reading them (nothing has to start at zero), so calls
- * whose work overlaps on the GPU (different streams, or different host
- * threads) race and must be serialised by the caller.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current) and caches it; make that first call before any
- * stream capture.  Work is enqueued on `stream`.                           */
+ * every device that loads the library until the process exits), worked
+ * through in chunks of blocks.  One block's scratch must fit it: the n x n
+ * Gram matrix (8 n^2 bytes for ZS_F64, 4 n^2 otherwise) and, for float
+ * factors with n >= 64, a subspace basis (about 8 n m bytes, m = k + 16
+ * rounded up to 8, at most 64) plus b x m projections and Rayleigh-Ritz
+ * data (about 4 m (b + m (b / 128 + 2)) bytes); sizes over that are rejected
+ * with ZS_EINVAL, whose message gives the bytes asked for.  The call makes
+ * no cudaMalloc, cudaFree or other allocating call.  Every call uses the
+ * same array and overwrites the parts it reads before reading them (nothing
+ * has to start at zero), so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture, and do not call it again on a
+ * device after cudaDeviceReset (the cached address is then stale).  Work is
+ * enqueued on `stream`; zs_noalloc_status reports how the last call went.  */
 zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_t ld, int32_t in_dtype, int64_t n,
                               int64_t b, int32_t k, int32_t flags, void* U, void* sigma, void* Vt,
                               void* stream);
+
+/* Status of the last zs_compress_noalloc call on the current device, read
+ * from two words in the same fixed device array (cleared by each call, so it
+ * allocates nothing either).  Synchronises the device.  *fault (host, may be
+ * NULL) is 1 if a bounded wait of a tensor-core kernel gave up (the factors
+ * are then undefined; returns ZS_ETIMEDOUT); *unconverged_blocks (may be
+ * NULL) counts blocks that did not pass the accuracy test of
+ * zs_store_status within its pass cap (returns ZS_ENOCONV); else ZS_OK.    */
+zs_status zs_noalloc_status(int32_t* fault, int32_t* unconverged_blocks);
 
 /* ------------------------------------------------------------------------
  * Query phase (Algorithm 2 with Partial-SVD Algorithm 3; Eq. 5-9).

@@ -229,6 +229,8 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.wst = st.w;
     a.w_rows = st.cap_blocks * st.cfg.k;
     a.fault = st.d_fault;
+    a.noconv = st.d_fault + 2;
+    a.refined = st.d_fault + 4;
     a.b = (int32_t)st.cfg.b;
     a.n = (int32_t)st.cfg.n;
     a.k = st.cfg.k;
@@ -313,8 +315,11 @@ static zs_status store_alloc(zs_store* st) {
     if ((s = al(&st->vt, ts * nb * c.k * c.n, "store V")) != ZS_OK) return s;
     if (use_tc_path(st->fp64, (int)c.n, c.flags))
         if ((s = al(&st->w, ts * nb * c.k * c.n, "store Sigma V^T")) != ZS_OK) return s;
-    if ((s = al((void**)&st->d_fault, sizeof(int), "fault word")) != ZS_OK) return s;
-    ZS_CU(cudaMemset(st->d_fault, 0, sizeof(int)), "memset");
+    // status words: [0] fault (a bounded wait gave up), [1] blocks and [2]
+    // queries whose refinement stopped at its pass cap, [3] blocks and [4]
+    // queries that needed refinement
+    if ((s = al((void**)&st->d_fault, 8 * sizeof(int), "status words")) != ZS_OK) return s;
+    ZS_CU(cudaMemset(st->d_fault, 0, 8 * sizeof(int)), "memset");
     if ((s = al(&st->tail, st->insize * (size_t)c.b * c.n, "open-block rows")) != ZS_OK) return s;
     // Gram scratch: chunk of blocks whose n x n Grams stay L2-sized
     const size_t gper = ts * (size_t)c.n * c.n;
@@ -501,6 +506,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
             ch.vt = st->vt;
             ch.w = st->w;
             ch.fault = st->d_fault;
+            ch.noconv = st->d_fault + 1;
+            ch.refined = st->d_fault + 3;
             ch.xi = st->xi;
             ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
             ch.ews = st->ews;
@@ -537,6 +544,8 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.vt = st->vt;
         ch.w = st->w;
         ch.fault = st->d_fault;
+        ch.noconv = st->d_fault + 1;
+        ch.refined = st->d_fault + 3;
         ch.xi = st->xi;
         ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
         ch.ews = st->ews;
@@ -726,6 +735,24 @@ extern "C" zs_status zs_store_fault(const zs_store* st, int32_t* flag) {
     int v = 0;
     ZS_CU(cudaMemcpy(&v, st->d_fault, sizeof(int), cudaMemcpyDeviceToHost), "fault word");
     *flag = v;
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_status(const zs_store* st, int64_t* unconverged_blocks, int64_t* unconverged_queries,
+                                     int64_t* refined_blocks, int64_t* refined_queries) {
+    if (!st) return fail(ZS_EINVAL, "null store");
+    DeviceGuard g(st->cfg.device);
+    ZS_CU(cudaDeviceSynchronize(), "status wait");
+    int v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    ZS_CU(cudaMemcpy(v, st->d_fault, sizeof v, cudaMemcpyDeviceToHost), "status words");
+    if (unconverged_blocks) *unconverged_blocks = v[1];
+    if (unconverged_queries) *unconverged_queries = v[2];
+    if (refined_blocks) *refined_blocks = v[3];
+    if (refined_queries) *refined_queries = v[4];
+    if (v[0]) return fail(ZS_ETIMEDOUT, "a bounded wait of a tensor-core kernel gave up; results are undefined");
+    if (v[1] || v[2])
+        return fail(ZS_ENOCONV, "%d block(s) and %d query result(s) did not pass the accuracy test within the pass cap",
+                    v[1], v[2]);
     return ZS_OK;
 }
 
@@ -986,6 +1013,7 @@ extern "C" const char* zs_status_str(zs_status s) {
         case ZS_ECUDA: return "CUDA error";
         case ZS_EINTERNAL: return "internal error";
         case ZS_ENOTFOUND: return "not found";
+        case ZS_ENOCONV: return "not converged";
     }
     return "unknown status";
 }

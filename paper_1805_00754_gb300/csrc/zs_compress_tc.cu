@@ -17,6 +17,8 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
     sc.power_its = tu.power_its;
     tc_aux_carve(c.aux, c.nblk, (int64_t)c.nblk * ((c.b + 127) / 128), sc.m, c.k, sc);
     sc.fault = c.fault;
+    sc.noconv = c.noconv;
+    sc.refined = c.refined;
     SrcCompress src{c};
     const bool aligned = (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) && (c.lda % 4 == 0);
     return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,

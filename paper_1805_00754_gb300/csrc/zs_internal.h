@@ -41,6 +41,8 @@ struct CompressChunk {
     void* ys;         // tensor path: nblk x b x 64 floats (Y = X Q~)
     void* aux;        // tensor path: tc_aux_bytes(nblk, nblk*ceil(b/128), m, k)
     int* fault;       // device word set to 1 when a bounded wait gives up (or null)
+    int* noconv;      // device count of blocks whose refinement stopped at its pass cap (or null)
+    int* refined;     // device count of blocks that needed refinement (or null)
     double xi;        // > 0: energy rule of Eq. 1 per block (rank k_i <= k), else fixed k
     double* energy;   // xi > 0: nblk doubles of scratch (each block's squared Frobenius norm)
 };
@@ -113,6 +115,8 @@ struct QueryArgs {
     void* aux;        // tensor path: tc_aux_bytes(nq, aux_tiles, m, kq)
     int64_t aux_tiles;
     int* fault;       // device word set to 1 when a bounded wait gives up (or null)
+    int* noconv;      // device count of queries whose refinement stopped at its pass cap (or null)
+    int* refined;     // device count of queries that needed refinement (or null)
 };
 
 // Launch configuration chosen by the autotuner (or defaults).

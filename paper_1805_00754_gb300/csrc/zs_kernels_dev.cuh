@@ -923,3 +923,4 @@ __global__ void __launch_bounds__(256) k_lift(QueryArgs a) {
 }  // namespace zs
 
 #include "zs_tc_kernels.cuh"
+#include "zs_certify.cuh"

@@ -39,7 +39,8 @@ static inline size_t tc_subspace_smem(int n, int m, bool& yglob) {
 }
 
 // Auxiliary scratch of the tensor path, carved from one buffer:
-// [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw]
+// [Hp: tiles x m x m | Cq: items x m x m | Zs: items x m x kw | th: items x kw |
+//  thm: items x m | list: 2 + items ints]
 
 static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, int kw, TcScratch& sc) {
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -51,6 +52,10 @@ static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, 
     sc.Zs = (float*)p;
     p += r(4 * (size_t)items * m * kw);
     sc.th = (float*)p;
+    p += r(4 * (size_t)items * kw);
+    sc.thm = (float*)p;
+    p += r(4 * (size_t)items * m);
+    sc.list = (int*)p;
 }
 
 // The sketch kernel covers n <= 512 with its accumulator S (n x m) held in
@@ -132,6 +137,62 @@ static bool t5_maps(const SrcQuery& s, int n, T5Maps& mp) {
     if (s.a.k % 8 != 0) return false;
     if (!t5_map(&mp.x0, s.a.M, s.a.m_rows, n, n, 8)) return false;
     return s.a.wst ? t5_map(&mp.x1, s.a.wst, s.a.w_rows, n, n, 8) : t5_map(&mp.x1, s.a.M, s.a.m_rows, n, n, 8);
+}
+
+// Accuracy test of every item's factors, then refinement of the items that
+// fail it (zs_certify.cuh).  The refinement needs n <= 512 (its basis and tiles
+// in shared memory); above that a failing item is counted as not converged.
+template <class Src, typename Tin>
+static cudaError_t certify_launch(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int num_sms,
+                                  cudaStream_t st) {
+    ZS_TRY(cudaMemsetAsync(sc.list, 0, 2 * sizeof(int), st));
+    {
+        const size_t sm = ck_smem_bytes(n, kw);
+        int dev = 0, smem_sm = 0, resv = 0;
+        ZS_TRY(cudaGetDevice(&dev));
+        ZS_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        ZS_TRY(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+        const int per_sm = std::max(1, std::min(4, smem_sm / (int)(sm + 1024 + resv)));
+        const int grid = std::max(1, std::min(max_items, num_sms * per_sm));
+        prof::Scope ps(std::is_same<Src, SrcQuery>::value ? "check_query" : "check", st);
+        auto go = [&](auto kern) -> cudaError_t {
+            ZS_TRY(set_smem(kern, sm));
+            kern<<<grid, 256, sm, st>>>(src, sc, n, kw);
+            return cudaGetLastError();
+        };
+        // 16-row tiles of R per warp: 1 (n <= 128), 2 (n <= 256), 4 (blocks of 512 columns)
+        const int ntw = n <= 128 ? 1 : (n <= 256 ? 2 : 4);
+        if (kw <= 16) {
+            if (ntw == 1) ZS_TRY(go(k_check<Src, Tin, 1, 2>));
+            else if (ntw == 2) ZS_TRY(go(k_check<Src, Tin, 2, 2>));
+            else ZS_TRY(go(k_check<Src, Tin, 4, 2>));
+        } else if (kw <= 32) {
+            if (ntw == 1) ZS_TRY(go(k_check<Src, Tin, 1, 4>));
+            else if (ntw == 2) ZS_TRY(go(k_check<Src, Tin, 2, 4>));
+            else ZS_TRY(go(k_check<Src, Tin, 4, 4>));
+        } else {
+            if (ntw == 1) ZS_TRY(go(k_check<Src, Tin, 1, 8>));
+            else if (ntw == 2) ZS_TRY(go(k_check<Src, Tin, 2, 8>));
+            else ZS_TRY(go(k_check<Src, Tin, 4, 8>));
+        }
+    }
+    {
+        prof::Scope ps(std::is_same<Src, SrcQuery>::value ? "refine_query" : "refine", st);
+        const int grid = std::max(1, std::min(max_items, num_sms));
+        const size_t sm = rf_smem_bytes(n);
+        if (n <= 256) {
+            ZS_TRY(set_smem(k_refine<Src, Tin, 1>, sm));
+            k_refine<Src, Tin, 1><<<grid, kRefineThreads, sm, st>>>(src, sc, n, kw);
+        } else if (n <= 512) {
+            ZS_TRY(set_smem(k_refine<Src, Tin, 2>, sm));
+            k_refine<Src, Tin, 2><<<grid, kRefineThreads, sm, st>>>(src, sc, n, kw);
+        } else {
+            k_count_listed<<<1, 32, 0, st>>>(sc.list, sc.noconv);
+        }
+        ZS_TRY(cudaGetLastError());
+    }
+    note_launches(2);
+    return cudaSuccess;
 }
 
 template <class Src, typename Tin, bool REF, bool QUERY>
@@ -220,6 +281,7 @@ static cudaError_t tc_core(const Src& src, TcScratch sc, int n, int kw, int max_
         k_rr_out<Src, QUERY><<<gi, 256, sm, st>>>(src, sc, n, kw);
     }
     ZS_TRY(cudaGetLastError());
+    ZS_TRY((certify_launch<Src, Tin>(src, sc, n, kw, max_items, num_sms, st)));
     note_launches(5);
     return cudaSuccess;
 }
@@ -313,6 +375,8 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             sc.power_its = tu.power_its;
             tc_aux_carve(a.aux, max_nq, a.aux_tiles, sc.m, kq, sc);
             sc.fault = a.fault;
+            sc.noconv = a.noconv;
+            sc.refined = a.refined;
             SrcQuery src{a};
             // stacked rows (M and the store's Sigma V^T) are 16-byte aligned when n % 4 == 0
             ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,

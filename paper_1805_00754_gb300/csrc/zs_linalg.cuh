@@ -80,7 +80,7 @@ struct JacobiScratch {
 // accumulated into the Z given (warm start / refinement).  Returns sweeps used.
 template <typename T>
 __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>& js,
-                          int max_sweeps, bool init_z) {
+                          int max_sweeps, bool init_z, int floor_mult = 64) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (init_z)
         for (int e = tid; e < m * m; e += nt) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
@@ -98,7 +98,8 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
     const T tol = T(64) * eps_of<T>();
     // absolute floor: in FP32 the updates leave noise ~eps * max|a_ii| in every
     // entry, so pairs between small eigenvalues would otherwise rotate forever
-    const T floor_ = (sizeof(T) == 4 ? T(64) : T(1)) * eps_of<T>() * js.scale;
+    // (floor_mult lowers it where the eigenvectors of small eigenvalues matter)
+    const T floor_ = (sizeof(T) == 4 ? T(floor_mult) : T(1)) * eps_of<T>() * js.scale;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) js.flag = 0;
@@ -338,8 +339,11 @@ __device__ void warp_sort_desc(const T* A, int lda, int m, int* perm) {
 // FP64 Rayleigh quotient Z^T A Z of FP32 eigenvectors Z): the rotations of a
 // Jacobi sweep over such a B have angles B_ij / (B_jj - B_ii) to first order,
 // so W = I + E with E_ij = B_ij / (B_jj - B_ii) (i != j), and the eigenvalues
-// to second order are B_jj + sum_i B_ij E_ij.  Pairs whose gap is at the
-// rounding level of B are left alone (any basis of a cluster is valid).  The
+// to second order are B_jj + sum_i B_ij E_ij.  E is skew-symmetric, so W is
+// orthogonal up to E^2: only pairs with |E_ij| <= 1e-3 are corrected, which
+// keeps the columns orthonormal to ~1e-6; the others (gaps within 1e3 |B_ij|,
+// where the FP32 rotations leave an eigenvalue error below B_ij^2 / gap) and
+// pairs whose gap is at the rounding level of B are left alone.  The
 // refined eigenvalues replace B's diagonal.  Called by all threads of a warp
 // (sync = __syncwarp) or a CTA (sync = __syncthreads); thread t0 of tn.
 template <typename T, typename Sync>
@@ -352,7 +356,7 @@ __device__ void refine_sweep(T* B, int ldb, T* W, int ldw, int m, int t0, int tn
             if (i != j) {
                 const T bij = B[i * ldb + j], bii = B[i * ldb + i];
                 const T gap = bjj - bii;
-                if (zabs(gap) > T(1e-9) * (zabs(bii) + zabs(bjj)) && zabs(bij) < T(0.25) * zabs(gap)) {
+                if (zabs(gap) > T(1e-9) * (zabs(bii) + zabs(bjj)) && zabs(bij) <= T(1e-3) * zabs(gap)) {
                     e = bij / gap;
                     corr += bij * e;
                 }

@@ -25,23 +25,36 @@ namespace {
 // process exits.
 constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+// Status words of the last call: [0] a bounded wait of a tensor-core kernel
+// gave up (results undefined), [1] blocks whose accuracy refinement stopped at
+// its pass cap.  Cleared at the start of every call.
+__device__ __align__(16) int g_noalloc_status[4];
 
-// Device address of the array, looked up once per device (host code may not use
-// the symbol itself as a device pointer).
+// Device addresses of the two arrays, looked up once per device with that
+// device current (host code may not use the symbols themselves as device
+// pointers).  They stay valid for the life of the device's primary context:
+// after cudaDeviceReset the module is loaded again at new addresses, so a
+// process that resets a device must not call zs_compress_noalloc on it again.
 constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
 void* g_addr[kMaxDevices] = {nullptr};
+int* g_stat[kMaxDevices] = {nullptr};
 
-zs_status scratch_address(int dev, void** out) {
+zs_status scratch_address(int dev, void** out, int** stat) {
     if (dev < 0 || dev >= kMaxDevices) return zs::fail(ZS_EINVAL, "device %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_addr_mu);
     if (!g_addr[dev]) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        void* q = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        e = cudaGetSymbolAddress(&q, g_noalloc_status);
+        if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetSymbolAddress(no-alloc status)");
         g_addr[dev] = p;
+        g_stat[dev] = (int*)q;
     }
     *out = g_addr[dev];
+    if (stat) *stat = g_stat[dev];
     return ZS_OK;
 }
 
@@ -61,7 +74,8 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetDevice");
     void* scratch = nullptr;
-    zs_status s = scratch_address(dev, &scratch);
+    int* stat = nullptr;
+    zs_status s = scratch_address(dev, &scratch, &stat);
     if (s != ZS_OK) return s;
     int num_sms = 1;
     e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -94,16 +108,21 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
     auto r256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t qper = tc ? r256(4 * zs::tc_qb_floats((int)mt, (int)n)) : 0;
     const size_t proj = r256(4 * mt * (size_t)b);
-    // Rayleigh-Ritz scratch of one block (tile partials, Q~^T Q~, Ritz data) with slack for alignment
-    const size_t auxp = tc ? r256(4 * mt * mt * ((b + 127) / 128 + 1) + 4 * mt * k + 4 * k + 1024) : 0;
+    // Rayleigh-Ritz scratch of one block (tile partials, Q~^T Q~, Ritz data,
+    // the accuracy test's list) with slack for the alignment of its sections
+    const size_t auxp = tc ? r256(4 * mt * mt * ((b + 127) / 128 + 1) + 4 * mt * k + 4 * k + 4 * mt + 4 + 2048) : 0;
     const size_t yper = proj + auxp;
     const size_t gper = ((ts * (size_t)n * n) + 255) & ~(size_t)255;
     if (ews_bytes + gper + qper + yper > kNoAllocScratchBytes)
-        return zs::fail(ZS_EINVAL, "n=%lld needs %zu scratch bytes per block; the no-alloc scratch holds %zu",
-                        (long long)n, ews_bytes + gper + qper + yper, kNoAllocScratchBytes);
+        return zs::fail(ZS_EINVAL,
+                        "n=%lld, b=%lld, k=%d need %zu scratch bytes per block (n x n Gram, and on the float tensor "
+                        "path a basis of n x %zu and b x %zu projections); the no-alloc scratch holds %zu",
+                        (long long)n, (long long)b, k, ews_bytes + gper + qper + yper, mt, mt, kNoAllocScratchBytes);
     const int chunk = (int)std::min<size_t>((kNoAllocScratchBytes - ews_bytes) / (gper + qper + yper), 65535);
     const int64_t nblk = (nrows + b - 1) / b;
     cudaStream_t st = (cudaStream_t)stream;
+    e = cudaMemsetAsync(stat, 0, 4 * sizeof(int), st);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "status clear");
     for (int64_t j0 = 0; j0 < nblk; j0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, nblk - j0);
         zs::CompressChunk ch;
@@ -127,8 +146,30 @@ extern "C" zs_status zs_compress_noalloc(const void* rows, int64_t nrows, int64_
         ch.U = (char*)U + ts * (size_t)j0 * b * k;
         ch.sig = (char*)sigma + ts * (size_t)j0 * k;
         ch.vt = (char*)Vt + ts * (size_t)j0 * k * n;
+        ch.fault = stat;
+        ch.noconv = stat + 1;
         e = zs::launch_compress(ch, fp64, flags, tune, num_sms, st);
         if (e != cudaSuccess) return zs::cuda_fail(e, "compression kernels");
     }
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_noalloc_status(int32_t* fault, int32_t* unconverged_blocks) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "cudaGetDevice");
+    void* scratch = nullptr;
+    int* stat = nullptr;
+    zs_status s = scratch_address(dev, &scratch, &stat);
+    if (s != ZS_OK) return s;
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return zs::cuda_fail(e, "status wait");
+    int v[4] = {0, 0, 0, 0};
+    e = cudaMemcpy(v, stat, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return zs::cuda_fail(e, "status read");
+    if (fault) *fault = v[0];
+    if (unconverged_blocks) *unconverged_blocks = v[1];
+    if (v[0]) return zs::fail(ZS_ETIMEDOUT, "a bounded wait of a tensor-core kernel gave up; results are undefined");
+    if (v[1]) return zs::fail(ZS_ENOCONV, "%d block(s) did not pass the accuracy test within the pass cap", v[1]);
     return ZS_OK;
 }

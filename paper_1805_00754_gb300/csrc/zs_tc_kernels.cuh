@@ -59,6 +59,21 @@ struct SrcCompress {
         scale = 1.f;
         return (const Tin*)x.base + (size_t)r * c.lda;
     }
+    // the factors the storage step wrote for item j: U rows (row stride kw),
+    // sigma (kw), V^T (kw x n); kcap = columns that can be nonzero
+    __device__ __forceinline__ float* u_out(int j, int kw) const {
+        return (float*)c.U + (size_t)(c.slot0 + j) * c.b * kw;
+    }
+    __device__ __forceinline__ float* sig_out(int j, int kw) const {
+        return (float*)c.sig + (size_t)(c.slot0 + j) * kw;
+    }
+    __device__ __forceinline__ float* vt_out(int j, int kw) const {
+        return (float*)c.vt + (size_t)(c.slot0 + j) * kw * c.n;
+    }
+    __device__ __forceinline__ float* w_out(int j, int kw) const {
+        return c.w ? (float*)c.w + (size_t)(c.slot0 + j) * kw * c.n : nullptr;
+    }
+    __device__ __forceinline__ int kcap(int j, int kw) const { return min(kw, min(rows(j), c.n)); }
     __device__ __forceinline__ int64_t tile0(int j) const { return (int64_t)j * ((c.b + 127) / 128); }
     __device__ __forceinline__ int64_t ntiles() const { return (int64_t)c.nblk * ((c.b + 127) / 128); }
     __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
@@ -99,6 +114,15 @@ struct SrcQuery {
         }
         return (const Tin*)x.base + (size_t)r * a.n;
     }
+    // the stitched factors of query q: U_r rows = the lift coefficients C
+    // (row stride kq), sigma (kq), V_r^T (kq x n); kcap from the plan
+    __device__ __forceinline__ float* u_out(int q, int kw) const {
+        return (float*)a.C + (size_t)a.plans[q].slab0 * a.k * kw;
+    }
+    __device__ __forceinline__ float* sig_out(int q, int kw) const { return (float*)a.sr + (size_t)q * kw; }
+    __device__ __forceinline__ float* vt_out(int q, int kw) const { return (float*)a.vr + (size_t)q * kw * a.n; }
+    __device__ __forceinline__ float* w_out(int, int) const { return nullptr; }
+    __device__ __forceinline__ int kcap(int q, int kw) const { return min(kw, a.plans[q].kcap); }
     __device__ __forceinline__ int64_t tile0(int q) const { return a.plans[q].pad0; }
     __device__ __forceinline__ int64_t ntiles() const { return a.hdr->ntiles_total; }
     __device__ __forceinline__ void tile_item(int64_t t, int& item, int& rt) const {
@@ -126,6 +150,10 @@ struct TcScratch {
     float* Cq;              // items x m x m: Q~^T Q~
     float* Zs;              // items x m x kw: Ritz coefficients
     float* th;              // items x kw: Ritz values (sigma^2)
+    float* thm;             // items x m: all m Ritz values, descending (accuracy test)
+    int* list;              // 2 + items ints: count, work counter, then the items that failed the accuracy test
+    int* noconv;            // incremented per item whose refinement stopped at its pass cap (or null)
+    int* refined;           // incremented per item refined (or null)
     int* fault;             // set to 1 by a kernel whose bounded wait gave up (or null)
 };
 
@@ -1441,6 +1469,8 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
             Zg[e] = (float)d;
         }
         for (int c = lane; c < kw; c += 32) sc.th[(size_t)item * kw + c] = (float)thd[c];
+        if (sc.thm)
+            for (int c = lane; c < m; c += 32) sc.thm[(size_t)item * m + c] = (float)thd[c];
         __syncwarp();
     }
 }
@@ -1520,6 +1550,7 @@ __global__ void __launch_bounds__(128) k_rr_core_reg(Src src, TcScratch sc, int 
                 if (i < m) Zg[i * kw + rk] = v[i];
             sc.th[(size_t)item * kw + rk] = al;
         }
+        if (sc.thm && rk < m) sc.thm[(size_t)item * m + rk] = al;
     }
 }
 

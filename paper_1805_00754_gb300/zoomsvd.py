@@ -21,7 +21,8 @@ ZS_FLAG_FP64_REFINE = 1
 ZS_FLAG_EXACT_GRAM = 2
 DTYPES = {"f64": ZS_F64, "f32": ZS_F32, "bf16": ZS_BF16}
 STATUS = {0: "ZS_OK", 1: "ZS_EINVAL", 2: "ZS_ERANGE", 3: "ZS_ENOMEM", 4: "ZS_EBUSY",
-          5: "ZS_ETIMEDOUT", 6: "ZS_EDTYPE", 7: "ZS_ECUDA", 8: "ZS_EINTERNAL", 9: "ZS_ENOTFOUND"}
+          5: "ZS_ETIMEDOUT", 6: "ZS_EDTYPE", 7: "ZS_ECUDA", 8: "ZS_EINTERNAL", 9: "ZS_ENOTFOUND",
+          10: "ZS_ENOCONV"}
 
 
 class ZsError(RuntimeError):
@@ -60,6 +61,8 @@ SIGNATURES = {
     "zs_store_reset": (C.c_int, [C.c_void_p]),
     "zs_store_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "zs_store_fault": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "zs_store_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int64)]),
     "zs_store_set_xi": (C.c_int, [C.c_void_p, C.c_double]),
     "zs_similar_ranges": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32),
@@ -68,6 +71,7 @@ SIGNATURES = {
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
     "zs_compress_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int64, C.c_int64,
                                       C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "zs_noalloc_status": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "zs_query": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(Result), C.c_void_p]),
     "zs_store_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "zs_query_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32, C.c_int32,
@@ -206,6 +210,21 @@ class Store:
         _check(lib().zs_store_fault(self._h, C.byref(f)))
         return f.value
 
+    def status(self, check: bool = True):
+        """(unconverged blocks, unconverged query results) since creation;
+        synchronises the device.  With check, a nonzero count raises ZsError
+        (ZS_ENOCONV) and a set fault word ZS_ETIMEDOUT."""
+        return self.status_counts(check)[:2]
+
+    def status_counts(self, check: bool = True):
+        """(unconverged blocks, unconverged queries, refined blocks, refined
+        queries) since creation, as zs_store_status reports them."""
+        v = [C.c_int64() for _ in range(4)]
+        st = lib().zs_store_status(self._h, *[C.byref(x) for x in v])
+        if check or st not in (0, 5, 10):
+            _check(st)
+        return tuple(x.value for x in v)
+
     def export_block(self, i: int, stream=None):
         U = torch.empty((self.b, self.k), dtype=self.fdtype, device=self.device)
         s = torch.empty((self.k,), dtype=self.fdtype, device=self.device)
@@ -317,3 +336,14 @@ def profile_table() -> dict:
         _check(lib().zs_profile_get(i, C.byref(name), C.byref(n), C.byref(ms)))
         out[name.value.decode()] = (n.value, ms.value)
     return out
+
+
+def noalloc_status(check: bool = True):
+    """(fault word, unconverged blocks) of the last zs_compress_noalloc call on
+    the current device; synchronises the device.  With check, a set fault word
+    raises ZS_ETIMEDOUT and unconverged blocks ZS_ENOCONV."""
+    f, u = C.c_int32(), C.c_int32()
+    st = lib().zs_noalloc_status(C.byref(f), C.byref(u))
+    if check or st not in (0, 5, 10):
+        _check(st)
+    return f.value, u.value

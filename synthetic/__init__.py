@@ -56,9 +56,10 @@ class Workload:
 
 # The five workloads the method is measured on (shapes follow the paper's
 # Section 5: b ~ 1e3, ranges 1e4..3.2e5 rows, few latent factors).  Where the
-# number of latent sinusoids is not fixed by the workload definition it is
-# k + 8, so that the kept rank k sits inside the signal and not in the noise
-# bulk (the paper picks k by the energy rule of Eq. 1 for the same reason).
+# workload definition does not fix the number of latent sinusoids s, s is
+# k + 8 (a few more factors than the kept rank, like sensor data whose energy
+# sits in a handful of components).  Spectra without a gap after k are drawn
+# by ``spectral_rows`` below; the tests run the method on both kinds.
 WORKLOADS = {
     "plain_f64": Workload(
         "plain_f64", SeriesSpec(20_000, 32, 6, 0.05, 0.0, SEED_BASE + 0),
@@ -155,3 +156,61 @@ def to_bf16_bits(x: np.ndarray) -> np.ndarray:
 
 def bf16_bits_to_f64(bits: np.ndarray) -> np.ndarray:
     return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# Rows with a prescribed spectrum (no gap after the kept rank).
+#
+# Each row is a_t = z_t D Q^T with z_t ~ N(0, I_n), D = diag(d_1..d_n) and Q a
+# seeded random orthogonal n x n matrix: a stationary multi-series whose
+# covariance Q D^2 Q^T has eigenvalues d_j^2, so every block of b >= n rows
+# has singular values close to sqrt(b) d_j, with no gap unless d has one.
+# Families of d_j (j = 1..n):
+#   "pow0.5"   j^-0.5             slow power decay
+#   "pow1"     j^-1               power decay
+#   "geo0.97"  0.97^j             geometric decay
+#   "flat64"   1 for j <= 64, then 0.05: 64 equal-strength directions (64
+#              near-equal signals) over a noise floor
+# --------------------------------------------------------------------------
+SPECTRA = ("pow0.5", "pow1", "geo0.97", "flat64")
+
+
+@dataclasses.dataclass(frozen=True)
+class SpectralSpec:
+    T: int
+    n: int
+    family: str
+    seed: int = SEED_BASE + 100
+
+
+def spectrum(family: str, n: int) -> np.ndarray:
+    j = np.arange(1, n + 1, dtype=np.float64)
+    if family == "pow0.5":
+        return j ** -0.5
+    if family == "pow1":
+        return 1.0 / j
+    if family == "geo0.97":
+        return 0.97 ** j
+    if family == "flat64":
+        return np.where(j <= 64, 1.0, 0.05)
+    raise ValueError(f"unknown spectrum family {family!r}")
+
+
+def spectral_rows(spec: SpectralSpec, r0: int = 0, r1: int | None = None,
+                  dtype=np.float64) -> np.ndarray:
+    """Rows [r0, r1) of the seeded T x n matrix with spectrum ``spec.family``."""
+    if r1 is None:
+        r1 = spec.T
+    if not (0 <= r0 <= r1 <= spec.T):
+        raise ValueError("row range out of bounds")
+    g = np.random.Generator(np.random.PCG64([spec.seed, 0x5BEC]))
+    Q, R = np.linalg.qr(g.standard_normal((spec.n, spec.n)))
+    Q *= np.sign(np.diag(R))[None, :]
+    M = spectrum(spec.family, spec.n)[:, None] * Q.T          # D Q^T
+    out = np.empty((r1 - r0, spec.n), dtype=dtype)
+    for c in range(r0 // CHUNK, (r1 + CHUNK - 1) // CHUNK):
+        lo, hi = c * CHUNK, min((c + 1) * CHUNK, spec.T)
+        Z = _chunk_rng(spec.seed, c, 3).standard_normal((hi - lo, spec.n))
+        a, z = max(lo, r0), min(hi, r1)
+        out[a - r0: z - r0] = Z[a - lo: z - lo] @ M
+    return out

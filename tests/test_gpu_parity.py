@@ -10,12 +10,9 @@ import torch
 
 import oracle
 import synthetic
-from tests._parity import compare_query, gpu_store, sigma_rel_err, _to_np
+from tests._parity import F32, F64, compare_query, gpu_store, sigma_rel_err, _to_np
 
 pytestmark = pytest.mark.gpu
-
-F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-10)
-F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=5e-4)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -68,7 +65,7 @@ def test_plain_query_paper_range(plain):
     torch.cuda.synchronize()
     ref = oracle.query(ost, ts, te)
     assert out.U.shape == (14_445, 8)
-    compare_query(out, ref, **F64, label="plain")
+    compare_query(out, ref, **F64, label="plain", ost=ost, ts=ts, te=te, min_pairs=8)
 
 
 def test_plain_edge_ranges(plain):
@@ -77,7 +74,8 @@ def test_plain_edge_ranges(plain):
         for kout in (1, w.k, 12):
             out = st.query(ts, te, kout)
             torch.cuda.synchronize()
-            compare_query(out, oracle.query(ost, ts, te, kout), **F64, label=f"[{ts},{te}] k{kout}")
+            compare_query(out, oracle.query(ost, ts, te, kout), **F64, label=f"[{ts},{te}] k{kout}",
+                          ost=ost, ts=ts, te=te)
 
 
 def test_lossless_matches_raw_range():
@@ -88,7 +86,8 @@ def test_lossless_matches_raw_range():
     for ts, te in [(1_234, 4_321), (0, 4_999), (250, 740), (777, 777), (4_500, 4_999)]:
         out = st.query(ts, te, 32)
         torch.cuda.synchronize()
-        compare_query(out, oracle.direct_svd(exact[ts:te + 1], 32), **F64, label=f"lossless [{ts},{te}]")
+        compare_query(out, oracle.direct_svd(exact[ts:te + 1], 32), **F64, label=f"lossless [{ts},{te}]",
+                      X=exact[ts:te + 1])
 
 
 def test_ragged_tail_and_piecewise_append():
@@ -113,7 +112,7 @@ def test_ragged_tail_and_piecewise_append():
         o2 = pieces.query(ts, te)
         torch.cuda.synchronize()
         assert torch.equal(o1.S, o2.S) and torch.equal(o1.U, o2.U) and torch.equal(o1.V, o2.V)
-        compare_query(o1, oracle.query(ost, ts, te), **F64, label=f"tail [{ts},{te}]")
+        compare_query(o1, oracle.query(ost, ts, te), **F64, label=f"tail [{ts},{te}]", ost=ost, ts=ts, te=te)
 
 
 def test_pipelined_small_appends_with_interleaved_queries():
@@ -132,7 +131,8 @@ def test_pipelined_small_appends_with_interleaved_queries():
         row += nb * w.b
         out = st.query(max(0, row - 3 * w.b // 2), row - 1)     # touches the newest blocks
         torch.cuda.synchronize()
-        compare_query(out, oracle.query(ost, max(0, row - 3 * w.b // 2), row - 1), **F32, label=f"pipe {row}")
+        a, z = max(0, row - 3 * w.b // 2), row - 1
+        compare_query(out, oracle.query(ost, a, z), **F32, label=f"pipe {row}", ost=ost, ts=a, te=z)
     assert st.info()[:2] == (A.shape[0], 9)
     for a, z in [(0, A.shape[0] - 1), (2_500, 13_333)]:
         o1, o2 = one.query(a, z), st.query(a, z)
@@ -150,7 +150,8 @@ def test_batch_equals_single(plain):
         torch.cuda.synchronize()
         assert torch.equal(one.S, outs[q].S) and torch.equal(one.U, outs[q].U) and torch.equal(one.V, outs[q].V)
     for q in range(0, 64, 8):
-        compare_query(outs[q], oracle.query(ost, int(ts[q]), int(te[q])), **F64, label=f"batch {q}")
+        compare_query(outs[q], oracle.query(ost, int(ts[q]), int(te[q])), **F64, label=f"batch {q}",
+                      ost=ost, ts=int(ts[q]), te=int(te[q]))
 
 
 def test_graph_replay_equals_eager():
@@ -228,7 +229,8 @@ def test_f32_compress_workload(refine):
     for a, z in list(zip(ts, te)) + _edge_ranges(T, w.b)[:6]:
         out = st.query(int(a), int(z))
         torch.cuda.synchronize()
-        compare_query(out, oracle.query(ost, int(a), int(z)), **F32, label=f"f32 [{a},{z}]")
+        compare_query(out, oracle.query(ost, int(a), int(z)), **F32, label=f"f32 [{a},{z}]", ost=ost, ts=int(a),
+                      te=int(z))
     assert st.fault() == 0          # no bounded wait of the tensor-core kernels gave up
 
 
@@ -244,8 +246,8 @@ def test_exact_gram_path_matches_oracle_and_tensor_path():
         o1, o2 = st_tc.query(a, z), st_ex.query(a, z)
         torch.cuda.synchronize()
         ref = oracle.query(ost, a, z)
-        compare_query(o1, ref, **F32, label=f"tensor [{a},{z}]")
-        compare_query(o2, ref, **F32, label=f"exact [{a},{z}]")
+        compare_query(o1, ref, **F32, label=f"tensor [{a},{z}]", ost=ost, ts=a, te=z)
+        compare_query(o2, ref, **F32, label=f"exact [{a},{z}]", ost=ost, ts=a, te=z)
 
 
 def test_bf16_precision_workload():
@@ -256,7 +258,7 @@ def test_bf16_precision_workload():
     for a, z in [(0, T - 1), (1_000, 7_000), (2_047, 2_048), (4_000, 9_999)]:
         out = st.query(a, z)
         torch.cuda.synchronize()
-        compare_query(out, oracle.query(ost, a, z), **F32, label=f"bf16 [{a},{z}]")
+        compare_query(out, oracle.query(ost, a, z), **F32, label=f"bf16 [{a},{z}]", ost=ost, ts=a, te=z)
 
 
 def test_ragged_batch_f32():
@@ -270,7 +272,7 @@ def test_ragged_batch_f32():
     worst = 0.0
     for q in range(len(ts)):
         ref = oracle.query(ost, int(ts[q]), int(te[q]))
-        compare_query(outs[q], ref, **F32, label=f"ragged {q}")
+        compare_query(outs[q], ref, **F32, label=f"ragged {q}", ost=ost, ts=int(ts[q]), te=int(te[q]))
         worst = max(worst, sigma_rel_err(outs[q], ref))
     assert worst <= 1e-4
     assert st.fault() == 0

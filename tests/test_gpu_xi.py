@@ -11,12 +11,9 @@ import torch
 
 import oracle
 import synthetic
-from tests._parity import compare_query, device_rows, _to_np
+from tests._parity import F32, F64, compare_query, device_rows, _to_np
 
 pytestmark = pytest.mark.gpu
-
-F64 = dict(s_tol=1e-10, vec_tol=1e-8, gap=1e-4, orth_tol=1e-10)
-F32 = dict(s_tol=1e-4, vec_tol=2e-3, gap=2e-2, orth_tol=5e-4)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,7 +64,7 @@ def test_xi_f64_plain_workload():
         r = int(np.count_nonzero(full.s))
         out = st.query(a, z, k_out=r)
         torch.cuda.synchronize()
-        compare_query(out, oracle.query(ost, a, z, k_out=r), **F64, label=f"xi f64 [{a},{z}]")
+        compare_query(out, oracle.query(ost, a, z, k_out=r), **F64, label=f"xi f64 [{a},{z}]", ost=ost, ts=a, te=z)
         res = st.query(a, z, k_out=w.k)
         torch.cuda.synchronize()
         tail = _to_np(res.S)
@@ -85,7 +82,7 @@ def test_xi_f32_tensor_path_ragged():
     for a, z in [(0, T - 1), (1_999, 2_000), (3_333, 12_345), (15_000, T - 1)]:
         out = st.query(a, z)
         torch.cuda.synchronize()
-        compare_query(out, oracle.query(ost, a, z), **F32, label=f"xi f32 [{a},{z}]")
+        compare_query(out, oracle.query(ost, a, z), **F32, label=f"xi f32 [{a},{z}]", ost=ost, ts=a, te=z)
     assert st.fault() == 0
 
 
