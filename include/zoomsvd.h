@@ -157,7 +157,10 @@ zs_status zs_store_fault(const zs_store* st, int32_t* flag);
  * R = X^T U from the factors as written, rho_j = |X^T u_j - sigma_j v_j|
  * and the bound beta_j = min(rho_j, rho_j^2 / (sigma_j - s_m)) on the
  * error of sigma_j (s_m the smallest Ritz value of the subspace), an item
- * passes when beta_j <= 1e-5 sigma_j for every kept pair.  Items that fail
+ * passes when beta_j <= 1e-5 max(sigma_j, 1e-2 sigma_1) for every kept
+ * pair (relative, and 1e-7 sigma_1 absolute for singular values below 1% of
+ * sigma_1, where FP32 arithmetic on the rows bounds what can be certified).
+ * Items that fail
  * are refined by subspace iteration (64 directions, at most 12 passes over
  * their rows); one that still fails keeps its last iterate and is counted
  * here.  Synchronises the device.  *unconverged_blocks and

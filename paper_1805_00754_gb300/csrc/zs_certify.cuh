@@ -18,8 +18,8 @@
 //             triplet, and its quadratic form, with the gap to the smallest
 //             Ritz value s_m of the subspace standing for the gap to the part
 //             of the spectrum the subspace does not hold.  An item passes when
-//             beta_j <= kCertTol sigma_j for every kept pair; the others are
-//             listed for refinement.
+//             beta_j <= kCertTol max(sigma_j, 1e-2 sigma_1) for every kept
+//             pair; the others are listed for refinement.
 //   k_refine  one CTA (16 warps) per listed item: subspace iteration of width
 //             kRefineM on X^T X, started from the sketch's basis plus random
 //             sign columns.  One pass over the item's rows per iteration gives
@@ -37,7 +37,7 @@
 
 namespace zs {
 
-constexpr float kCertTol = 1e-5f;       // bound on |sigma_j - sigma_j(X)| / sigma_j
+constexpr float kCertTol = 1e-5f;       // bound on |sigma_j - sigma_j(X)| / max(sigma_j, 1e-2 sigma_1)
 constexpr int kRefineMaxPasses = 16;    // passes over an item's rows in k_refine
 constexpr int kRefineM = 64;            // width of the refinement subspace (<= n on the tensor path)
 constexpr int kRefineThreads = 512;
@@ -51,7 +51,10 @@ __host__ __device__ __forceinline__ int ck_rows(int n) {
 }
 // strides = 8 mod 32: the transposed-operand fragments (rows t4, columns g) are conflict-free
 __host__ __device__ __forceinline__ int ck_ldx(int n) { return (n + 31) / 32 * 32 + 8; }
-__host__ __device__ __forceinline__ int ck_ldb(int w) { return (w + 31) / 32 * 32 + 8; }
+__host__ __device__ __forceinline__ int ck_ldb(int w) {        // = 8 or 24 mod 32
+    const int wp = (w + 7) / 8 * 8;
+    return wp + (((wp / 8) % 2 == 0) ? 8 : 16);
+}
 __host__ __device__ __forceinline__ size_t ck_stage_floats(int n, int kw) {
     return (size_t)ck_rows(n) * ck_ldx(n) + (size_t)ck_rows(n) * ck_ldb(kw);
 }
@@ -82,6 +85,21 @@ __device__ __forceinline__ void ld_xtile(const Src& src, const typename Src::Ctx
                                          int n, int ncp, float* Xs, int ldx, bool vec) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if constexpr (std::is_same<Tin, float>::value) {
+        if (vec && nt % (ncp / 4) == 0) {
+            // each thread keeps one 16-byte column piece and steps through the rows
+            const int q4 = ncp / 4, c = (tid % q4) * 4, rstep = nt / q4;
+            const bool live_c = c < n;
+            for (int r = tid / q4; r < nr; r += rstep) {
+                float* d = Xs + r * ldx + c;
+                if (r0 + r < rows && live_c) {
+                    float s;
+                    cp_async16(d, src.template row<float>(cx, r0 + r, s) + c, 16);
+                } else {
+                    *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            return;
+        }
         if (vec) {
             const int q4 = ncp / 4;
             for (int f = tid; f < nr * q4; f += nt) {
@@ -138,15 +156,20 @@ __device__ __forceinline__ bool rows_vec16(const Src& src, int item, int n) {
 }
 
 // Pass/fail rule shared by both kernels (thread 0): sig[j] the kept singular
-// values (0 = dropped), rho[j] the residual norms, sm the smallest Ritz value.
+// values (0 = dropped, sig[0] the largest), rho[j] the residual norms, sm the
+// smallest Ritz value.  The bound must stay below kCertTol max(sigma_j,
+// 1e-2 sigma_1): relative for sigma_j >= 1e-2 sigma_1, and 1e-7 sigma_1
+// absolute below that, where FP32 products of the rows (error ~ eps sigma_1)
+// leave no relative accuracy to certify.
 __device__ __forceinline__ bool cert_pass(const float* sig, const float* rho, int kc, float sm) {
     bool ok = true;
+    const float floor_ = 1e-2f * sig[0];
     for (int j = 0; j < kc; ++j) {
         const float sj = sig[j];
         if (!(sj > 0.f)) continue;
         const float r = rho[j], eta = sj - sm;
         const float beta = eta > 0.f ? fminf(r, r * r / eta) : r;
-        if (!(beta <= kCertTol * sj)) ok = false;          // a NaN fails
+        if (!(beta <= kCertTol * fmaxf(sj, floor_))) ok = false;          // a NaN fails
     }
     return ok;
 }
@@ -157,7 +180,8 @@ __device__ __forceinline__ bool cert_pass(const float* sig, const float* rho, in
 // over the item's rows; rho_j^2 accumulates over the blocks.
 // ---------------------------------------------------------------------------
 template <class Src, typename Tin, int NTW, int KT>
-__global__ void __launch_bounds__(256, (NTW * KT <= 8) ? 2 : 1) k_check(Src src, TcScratch sc, int n, int kw) {
+__global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 2 : 1))
+    k_check(Src src, TcScratch sc, int n, int kw) {
     extern __shared__ __align__(16) float cks[];
     __shared__ float s_sig[ZS_MAXM];
     __shared__ float s_rho[ZS_MAXM];
@@ -189,13 +213,13 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 8) ? 2 : 1) k_check(Src src,
         }
         const int ntl = (rows + TR - 1) / TR;
         for (int mt0 = 0; mt0 < nmt; mt0 += 8 * NTW) {
-            float acc[NTW][KT][4];
+            float acc[NTW][KT][4], acx[NTW][KT][4];
 #pragma unroll
             for (int a = 0; a < NTW; ++a)
 #pragma unroll
                 for (int b = 0; b < KT; ++b)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+                    for (int c = 0; c < 4; ++c) acc[a][b][c] = acx[a][b][c] = 0.f;
             auto issue = [&](int t) {
                 float* Xs = cks + (size_t)(t % nst) * sf;
                 ld_xtile<Src, Tin>(src, cx, t * TR, TR, rows, n, ncp, Xs, ldx, vec);
@@ -215,13 +239,14 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 8) ? 2 : 1) k_check(Src src,
                 __syncthreads();
                 const float* Xs = cks + (size_t)(t % nst) * sf;
                 const float* Bs = Xs + (size_t)TR * ldx;
+#pragma unroll 2
                 for (int k0 = 0; k0 < TR; k0 += 8) {
                     uint32_t bh[KT][2], bl[KT][2];
 #pragma unroll
                     for (int nt = 0; nt < KT; ++nt) {
                         if (nt >= nkt) break;
-                        tf32_split(Bs[(k0 + t4) * ldb + nt * 8 + g], bh[nt][0], bl[nt][0]);
-                        tf32_split(Bs[(k0 + t4 + 4) * ldb + nt * 8 + g], bh[nt][1], bl[nt][1]);
+                        tf32_split_trunc(Bs[(k0 + t4) * ldb + nt * 8 + g], bh[nt][0], bl[nt][0]);
+                        tf32_split_trunc(Bs[(k0 + t4 + 4) * ldb + nt * 8 + g], bh[nt][1], bl[nt][1]);
                     }
 #pragma unroll
                     for (int mi = 0; mi < NTW; ++mi) {
@@ -237,8 +262,9 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 8) ? 2 : 1) k_check(Src src,
 #pragma unroll
                         for (int nt = 0; nt < KT; ++nt) {
                             if (nt >= nkt) break;
-                            mma_tf32(acc[mi][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
-                            mma_tf32(acc[mi][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
+                            // the cross terms in their own accumulator: two independent chains
+                            mma_tf32(acx[mi][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
+                            mma_tf32(acx[mi][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
                             mma_tf32(acc[mi][nt], ah0, ah1, ah2, ah3, bh[nt][0], bh[nt][1]);
                         }
                     }
@@ -262,7 +288,7 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 8) ? 2 : 1) k_check(Src src,
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int i = mt * 16 + g + ((e >> 1) ? 8 : 0), j = nt * 8 + 2 * t4 + (e & 1);
-                        if (i < n) Rs[(i - i0) * ldr + j] = acc[mi][nt][e];
+                        if (i < n) Rs[(i - i0) * ldr + j] = acc[mi][nt][e] + acx[mi][nt][e];
                     }
                 }
             }
@@ -473,7 +499,9 @@ __global__ void __launch_bounds__(kRefineThreads, 1) k_refine(Src src, TcScratch
             }
             __syncthreads();
             // ---- Rayleigh-Ritz on span(Q) (Q orthonormal): H = Z Theta Z^T
-            jacobi_eig<float>(Hs, LH, Zs, LH, MR, js, 40, true, 4);
+            // relative convergence test only (floor 1e-14 lambda_1, below the
+            // rank tolerance): the small Ritz values keep their relative accuracy
+            jacobi_eig<float>(Hs, LH, Zs, LH, MR, js, 40, true, 1e-7f);
             sort_desc<float>(Hs, LH, MR, perm);
             if (tid < MR) s_th[tid] = fmaxf(Hs[perm[tid] * LH + perm[tid]], 0.f);
             __syncthreads();

@@ -80,7 +80,7 @@ struct JacobiScratch {
 // accumulated into the Z given (warm start / refinement).  Returns sweeps used.
 template <typename T>
 __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>& js,
-                          int max_sweeps, bool init_z, int floor_mult = 64) {
+                          int max_sweeps, bool init_z, T floor_mult = T(64)) {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (init_z)
         for (int e = tid; e < m * m; e += nt) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
@@ -98,8 +98,10 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
     const T tol = T(64) * eps_of<T>();
     // absolute floor: in FP32 the updates leave noise ~eps * max|a_ii| in every
     // entry, so pairs between small eigenvalues would otherwise rotate forever
-    // (floor_mult lowers it where the eigenvectors of small eigenvalues matter)
-    const T floor_ = (sizeof(T) == 4 ? T(floor_mult) : T(1)) * eps_of<T>() * js.scale;
+    // (floor_mult lowers it where small eigenvalues must keep their relative
+    // accuracy: the off-diagonals of an accurately formed graded matrix shrink
+    // with its diagonal, and the relative test alone converges)
+    const T floor_ = (sizeof(T) == 4 ? floor_mult : T(1)) * eps_of<T>() * js.scale;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         if (tid == 0) js.flag = 0;
