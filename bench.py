@@ -131,29 +131,22 @@ def _input_rows(w, host=False):
 # ----------------------------------------------------------------------------
 # CPU oracle (reference arm / cpu_baseline)
 # ----------------------------------------------------------------------------
-def oracle_sample(w, budget_s: float, rng_seed: int = 0):
-    """Time the FP64 oracle on a bounded sample of the workload: compress the
-    first blocks until about budget_s/2 has passed, then answer queries drawn
-    over the compressed sample for the rest.  Returns a dict of rates."""
+def oracle_sample(w, A, budget_s: float, rng_seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of the workload's rows A (as
+    the GPU reads them): compress the first blocks until about budget_s/2 has
+    passed, then answer queries drawn over the compressed sample for the
+    rest.  Returns a dict of rates."""
     import oracle
-    try:
-        import threadpoolctl
-        cores = max(p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()) or os.cpu_count()
-    except Exception:
-        cores = os.cpu_count()
+    cores = os.cpu_count()
     b, n, k = w.b, w.series.n, w.k
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
-    # compress blocks one by one (bounded)
     blocks, nb, tc = [], 0, 0.0
     nb_max = w.series.T // b
     while nb < nb_max and tc < budget_s / 2:
-        A = synthetic.rows(w.series, nb * b, (nb + 1) * b)
-        if w.dtype == "f32":
-            A = A.astype(np.float32).astype(np.float64)
-        elif w.dtype == "bf16":
-            A = synthetic.bf16_bits_to_f64(synthetic.to_bf16_bits(A))
+        R = A[nb * b: (nb + 1) * b]
+        Ab = synthetic.bf16_bits_to_f64(R.view(np.uint16)) if w.dtype == "bf16" else np.asarray(R, np.float64)
         tb = time.perf_counter()
-        blocks.append(oracle.compress_block(A, k))   # only the oracle's work is timed
+        blocks.append(oracle.compress_block(Ab, k))   # only the oracle's work is timed
         tc += time.perf_counter() - tb
         nb += 1
     st = oracle.Store(b=b, n=n, k=k, T=nb * b, U=[x[0] for x in blocks], s=[x[1] for x in blocks],
@@ -171,14 +164,148 @@ def oracle_sample(w, budget_s: float, rng_seed: int = 0):
             "compress_s": tc, "query_s": tq}
 
 
+class SharedRows:
+    """The workload's rows (as the GPU reads them) in a shared-memory segment,
+    so that the oracle's worker processes read them without copies."""
+
+    def __init__(self, A: np.ndarray, dtype: str):
+        from multiprocessing import shared_memory
+        self.shm = shared_memory.SharedMemory(create=True, size=max(A.nbytes, 1))
+        np.ndarray(A.shape, dtype=A.dtype, buffer=self.shm.buf)[...] = A
+        self.spec = (self.shm.name, A.shape, A.dtype.str, dtype)
+
+    def close(self):
+        self.shm.close()
+        self.shm.unlink()
+
+
+def _rows_from(spec, r0, r1):
+    """Rows [r0, r1) of a SharedRows segment, upcast exactly to FP64."""
+    from multiprocessing import shared_memory
+    name, shape, dt, kind = spec
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        A = np.ndarray(shape, dtype=np.dtype(dt), buffer=shm.buf)[r0:r1]
+        if kind == "bf16":
+            return synthetic.bf16_bits_to_f64(A.view(np.uint16))
+        return np.array(A, dtype=np.float64)
+    finally:
+        shm.close()
+
+
+def _pool_compress(job):
+    """Worker: compress blocks [i0, i1) (b rows each, the last one possibly
+    short) with the oracle; returns the factors and the seconds spent in the
+    oracle itself."""
+    import oracle
+    spec, b, k, T, i0, i1 = job
+    A = _rows_from(spec, i0 * b, min(i1 * b, T))
+    out, t = [], 0.0
+    for i in range(i0, i1):
+        Ab = A[(i - i0) * b: min((i - i0 + 1) * b, A.shape[0])]
+        t0 = time.perf_counter()
+        out.append(oracle.compress_block(Ab, k))
+        t += time.perf_counter() - t0
+    return i0, out, t
+
+
+def _pool_queries(job):
+    """Worker: answer queries with the oracle until `budget` seconds pass."""
+    import oracle
+    st, ts, te, budget = job
+    t0, nq = time.perf_counter(), 0
+    while nq < len(ts) and time.perf_counter() - t0 < budget:
+        oracle.query(st, int(ts[nq]), int(te[nq]))
+        nq += 1
+    return nq, time.perf_counter() - t0
+
+
+def oracle_pool(workers: int, one_thread: bool = True):
+    """A process pool (spawn) for the oracle; with one_thread each worker's
+    BLAS uses one thread, so the pool's width is the cores used."""
+    import multiprocessing as mp
+    keep = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    if one_thread:
+        for v in keep:
+            os.environ[v] = "1"
+    try:
+        return mp.get_context("spawn").Pool(workers)
+    finally:
+        for v, x in keep.items():
+            if x is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = x
+
+
+def oracle_compress_all(pool, spec, w, T, workers):
+    """Compress every block of the first T rows on the pool; returns (oracle
+    store, wall seconds)."""
+    import oracle
+    nb = (T + w.b - 1) // w.b
+    step = max(1, (nb + 4 * workers - 1) // (4 * workers))
+    jobs = [(spec, w.b, w.k, T, i, min(i + step, nb)) for i in range(0, nb, step)]
+    t0 = time.perf_counter()
+    res = sorted(pool.map(_pool_compress, jobs), key=lambda r: r[0])
+    wall = time.perf_counter() - t0
+    blocks = [x for _, out, _ in res for x in out]
+    st = oracle.Store(b=w.b, n=w.series.n, k=w.k, T=T, U=[x[0] for x in blocks], s=[x[1] for x in blocks],
+                      Vt=[x[2] for x in blocks])
+    return st, wall
+
+
+def cpu_baseline_sample(spec, w, budget_s: float, cores: int):
+    """The oracle as it stands, on this host: storage phase over the first
+    blocks and queries over them, on one core and on `cores` cores (a spawn
+    pool, one BLAS thread per worker).  Each of the four timings is bounded by
+    about budget_s / 4 seconds of CPU work."""
+    import oracle
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    b, n, T = w.b, w.series.n, w.series.T
+    out = {}
+    one = oracle_pool(1)
+    try:
+        nb, t, blocks = 0, 0.0, []
+        while t < budget_s / 4 and nb < T // b:
+            _, o, dt = one.map(_pool_compress, [(spec, b, w.k, T, nb, nb + 1)])[0]
+            blocks += o
+            t += dt
+            nb += 1
+        out["one_core"] = {"compress_gbps": nb * b * n * itemsize / t / 1e9, "blocks": nb}
+        qst = oracle.Store(b=b, n=n, k=w.k, T=nb * b, U=[x[0] for x in blocks], s=[x[1] for x in blocks],
+                           Vt=[x[2] for x in blocks])
+        ts, te = synthetic.queries(nb * b, 2_000, min(w.lmin or 1_000, nb * b), min(w.lmax or nb * b, nb * b),
+                                   seed=3)
+        nq, tq = one.map(_pool_queries, [(qst, ts, te, budget_s / 4)])[0]
+        out["one_core"].update({"queries_per_s": nq / tq, "queries": nq,
+                                "query_lengths": [int(np.min(te - ts + 1)), int(np.max(te - ts + 1))]})
+    finally:
+        one.close()
+    pool = oracle_pool(cores)
+    try:
+        nb = min(T // b, max(1, out["one_core"]["blocks"]) * cores)
+        _, wall = oracle_compress_all(pool, spec, w, nb * b, cores)
+        out["all_cores"] = {"compress_gbps": nb * b * n * itemsize / wall / 1e9, "blocks": nb}
+        chunks = [(qst, ts[i::cores], te[i::cores], budget_s / 4) for i in range(cores)]
+        t0 = time.perf_counter()
+        res = pool.map(_pool_queries, chunks)
+        wall = time.perf_counter() - t0
+        out["all_cores"].update({"queries_per_s": sum(r[0] for r in res) / wall,
+                                 "queries": sum(r[0] for r in res)})
+    finally:
+        pool.close()
+    return out
+
+
 def run_reference(args, w):
     ws, rank, _ = _dist()
     if rank != 0:
         return
     per_step = []
     last = None
+    A = _input_rows(w)
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(w, args.ref_budget, rng_seed=i)
+        r = oracle_sample(w, A, args.ref_budget, rng_seed=i)
         if i >= args.warmup:
             per_step.append(r)
         last = r
@@ -249,7 +376,7 @@ def kernel_model(name, w, launches_per_step, nq_total_rows, union_u_rows):
     """Compulsory bytes per launch of a kernel, for the roofline object."""
     itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
     T, n, b, k = w.series.T, w.series.n, w.b, w.k
-    if name in ("gram_compress", "form_u", "gram_lo", "project", "sketch"):
+    if name in ("gram_compress", "form_u", "gram_lo", "project", "sketch", "check"):
         # every input byte read once per launch set
         return "hbm", T * n * itemsize / launches_per_step
     if name == "lift":
@@ -339,6 +466,23 @@ def run_gpu(args, w):
     qps = aggregate_rate(ws, K, nq, tq) if nq else None
     ms_step = (tc + tq) / K * 1e3
 
+    status = st.status_counts(check=False)
+
+    # the same batch with U left factored (Sigma, V and per-block coefficients)
+    qps_fac = None
+    if nq:
+        fac = st.query_batch_factored(ts, te, k)          # warm (allocation, first launches)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(K):
+            st.query_batch_factored(ts, te, k, out=fac)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        (tf,) = reduce_max([f0.elapsed_time(f1) / 1e3], f"cuda:{local}")
+        qps_fac = aggregate_rate(ws, K, nq, tf)
+        del fac
+
     # e2e through the C ABI from pinned host rows (H2D inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -358,8 +502,20 @@ def run_gpu(args, w):
             if i >= args.warmup:
                 te2e += e0.elapsed_time(e1) / 1e3
         (te2e,) = reduce_max([te2e], f"cuda:{local}")
+        # a plain pinned host -> device copy of the same bytes on this machine (best of 3)
+        scratch = torch.empty_like(rows_dev)
+        best = None
+        for _ in range(3):
+            e0.record(stream)
+            scratch.copy_(host, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del scratch
         e2e = {"value": aggregate_rate(ws, K, in_bytes, te2e) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": k * (8 if w.dtype == "f64" else 4)}
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": k * (8 if w.dtype == "f64" else 4),
+               "pinned_h2d_copy_gbps": in_bytes / (best / 1e3) / 1e9}
 
     # roofline of the dominant kernel
     peaks, src = _peaks()
@@ -380,9 +536,39 @@ def run_gpu(args, w):
                     "traffic": None, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_step}
     kernels = {nm: {"launches": v[0], "ms_per_step": v[1] / K} for nm, v in table.items()}
 
+    # Theorem 3: the stored factors against the raw rows
+    _, nblk, fbytes = st.info()
+    space = {"factor_bytes": fbytes, "raw_bytes": in_bytes, "ratio": fbytes / in_bytes,
+             "per_block": f"b*k + k + k*n = {b * k + k + k * n} factor elements"}
+
+    plain32 = None
+    if rank == 0 and not args.skip_plain and nq:
+        plain32 = plain_fp32_run(st, ts, te, k)
     acc = None
-    if rank == 0 and not args.skip_accuracy and nq:
-        acc = accuracy_sample(st, w, A)
+    cpu = None
+    if rank == 0 and (not args.skip_accuracy or not args.skip_cpu):
+        cores = os.cpu_count() or 1
+        shared = SharedRows(A, w.dtype)
+        try:
+            if not args.skip_accuracy and nq:
+                pool = oracle_pool(cores)
+                try:
+                    ost, _ = oracle_compress_all(pool, shared.spec, w, T, cores)
+                finally:
+                    pool.close()
+                acc = accuracy_sample(st, w, ost)
+                del ost
+            r = cpu_baseline_sample(shared.spec, w, args.cpu_budget, cores) if (not args.skip_cpu and ws == 1) \
+                else None
+        finally:
+            shared.close()
+        if r is not None:
+            cpu = {"value": r["all_cores"]["compress_gbps"], "unit": "GB/s", "cores": cores, "kind": "oracle",
+                   "sample": (f"oracle storage phase over the first {r['all_cores']['blocks']} blocks on {cores} "
+                              f"worker processes (one BLAS thread each) and over {r['one_core']['blocks']} blocks "
+                              f"on one; queries log-uniform over the compressed rows; "
+                              f"~{args.cpu_budget:.0f} s of CPU in all"),
+                   "one_core": r["one_core"], "all_cores": r["all_cores"]}
     plain = None
     if rank == 0 and not args.skip_plain and nq:
         st.close()
@@ -391,14 +577,7 @@ def run_gpu(args, w):
         plain = plain_fp64_run(w, A, ts, te, local)
     serving = None
     if args.serve_seconds > 0 and rank == 0:
-        serving = serve_run(args.serve_seconds, local)
-    cpu = None
-    if rank == 0 and ws == 1 and not args.skip_cpu:
-        r = oracle_sample(w, args.cpu_budget)
-        cpu = {"value": r["compress_gbps"], "unit": "GB/s", "cores": r["cores"], "kind": "oracle",
-               "sample": f"oracle compressed the first {r['blocks']} blocks ({r['compress_s']:.1f} s) and answered "
-                         f"{r['queries']} queries over them ({r['query_s']:.1f} s); queries/s "
-                         f"{r['queries_per_s']:.3g}"}
+        serving = serve_run(args.serve_seconds, local, warmup=args.serve_warmup)
     if rank == 0:
         line = {"metric": METRIC, "value": compress_gbps, "unit": "GB/s", "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -408,10 +587,19 @@ def run_gpu(args, w):
                            "queries_per_step": nq, "query_rows_per_step": out_rows,
                            "l2": "inputs larger than L2 (no flush needed)",
                            "parallelism": f"replicas x{ws}"},
-                "queries_per_s": qps, "compress_s_per_step": tc / K, "query_s_per_step": tq / K,
-                "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"],
-                "accuracy": acc, "serving": serving, "plain_fp64_gpu": plain,
-                "queries_per_s_vs_plain": (qps / plain["queries_per_s"]) if (plain and qps) else None,
+                "queries_per_s": qps, "queries_per_s_factored": qps_fac,
+                "compress_s_per_step": tc / K, "query_s_per_step": tq / K,
+                "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"], "space": space,
+                "accuracy_test": {"unconverged_blocks": status[0], "unconverged_queries": status[1],
+                                  "refined_blocks": status[2], "refined_queries": status[3]},
+                "accuracy": acc, "serving": serving,
+                "plain_fp32_gpu": plain32,
+                "queries_per_s_vs_plain_fp32": (qps / plain32["queries_per_s"]) if (plain32 and qps) else None,
+                "plain_fp64_gpu": plain,
+                "queries_per_s_vs_plain_fp64": (qps / plain["queries_per_s"]) if (plain and qps) else None,
+                "comparisons": "vs_plain_fp32: equal precision (the same FP32 store, one query per call); "
+                               "vs_plain_fp64: unequal precision (FP32 batched, sigma error <= 1e-4, against "
+                               "FP64 one query per call, sigma error ~1e-15)",
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -535,46 +723,85 @@ def plain_fp64_run(w, A, ts, te, local, budget_s=4.0, acc_queries=3):
             "compress_gbps_of_input": T * n * itemsize / tc / 1e9, "sigma_max_rel_err": worst}
 
 
-def accuracy_sample(st, w, A, nq=4, max_len=20_000, seed=7):
-    """sigma / subspace error of a few GPU query results against the FP64
-    oracle run on the same (dtype-rounded) rows; only the covered blocks are
-    compressed by the oracle."""
+def accuracy_sample(st, w, ost, nq=8, seed=synthetic.SEED_BASE + 98):
+    """Errors of GPU query results against the FP64 oracle run on the same
+    (dtype-rounded) rows, at the bench's own range lengths (nq ranges drawn
+    like the timed batch).  Per query: the worst relative error of sigma, the
+    sine of the largest principal angle between the device's and the
+    oracle's V, the truncation gap sigma_k / sigma_k+1 of the range (oracle),
+    and the Wedin bound sqrt(2) |R|_F / (sigma_k - sigma_k+1) on that angle
+    implied by the device pairs' residuals R against the oracle's range."""
     import oracle
     import torch
     T, b, k = w.series.T, w.b, w.k
-    ts, te = synthetic.queries(T, nq, 2 * b, max_len, seed=seed)
-    worst_s, worst_sin = 0.0, 0.0
+    ts, te = synthetic.queries(T, nq, w.lmin or 1_000, w.lmax or T, seed=seed)
+    per, worst_s, worst_sin = [], 0.0, 0.0
     for a, z in zip(ts, te):
-        S, E = int(a) // b, int(z) // b
-        rows = A[S * b: min((E + 1) * b, T)]
-        if w.dtype == "bf16":
-            exact = synthetic.bf16_bits_to_f64(rows.view(np.uint16))
-        else:
-            exact = np.asarray(rows, dtype=np.float64)
-        ost = oracle.compress(exact, b, k)
-        ref = oracle.query(ost, int(a) - S * b, int(z) - S * b)
-        out = st.query(int(a), int(z))
+        a, z = int(a), int(z)
+        ref = oracle.query(ost, a, z)
+        out = st.query(a, z)
         torch.cuda.synchronize()
         s = out.S.cpu().numpy().astype(np.float64)
+        U = out.U.cpu().numpy().astype(np.float64)
+        V = out.V.cpu().numpy().astype(np.float64)
         m = ref.s > 0
-        worst_s = max(worst_s, float(np.max(np.abs(s[m] - ref.s[m]) / ref.s[m])))
-        V = out.V.cpu().numpy().astype(np.float64)[:, m]
-        Q1, _ = np.linalg.qr(V)
+        es = float(np.max(np.abs(s[m] - ref.s[m]) / ref.s[m]))
+        Q1, _ = np.linalg.qr(V[:, m])
         Q2, _ = np.linalg.qr(ref.V[:, m])
-        worst_sin = max(worst_sin, float(np.linalg.norm(Q2 - Q1 @ (Q1.T @ Q2), 2)))
+        sin = float(np.linalg.norm(Q2 - Q1 @ (Q1.T @ Q2), 2))
+        # residuals against the oracle's range matrix and its full spectrum
+        r = int(np.sum(m))
+        AtU = np.zeros((w.series.n, r))
+        AV = np.zeros((z - a + 1, r))
+        G = np.zeros((w.series.n, w.series.n))
+        for i in range(a // b, z // b + 1):
+            lo = i * b
+            Ai = (ost.U[i][max(a, lo) - lo: min(z + 1, lo + b) - lo] * ost.s[i][None, :]) @ ost.Vt[i]
+            AtU += Ai.T @ U[max(a, lo) - a: min(z + 1, lo + b) - a, :r]
+            AV[max(a, lo) - a: min(z + 1, lo + b) - a] = Ai @ V[:, :r]
+            G += Ai.T @ Ai
+        full = np.sqrt(np.maximum(np.linalg.eigvalsh(G)[::-1], 0.0))
+        R2 = np.sum((AtU - V[:, :r] * s[None, :r]) ** 2) + np.sum((AV - U[:, :r] * s[None, :r]) ** 2)
+        gap = full[r - 1] - full[r] if full.size > r else full[r - 1]
+        wedin = float(np.sqrt(2.0 * R2) / gap) if gap > 0 else None
+        per.append({"rows": z - a + 1, "sigma_rel_err": es, "v_sin": sin,
+                    "gap_k": float(full[r - 1] / full[r]) if full.size > r and full[r] > 0 else None,
+                    "wedin_bound": wedin})
+        worst_s, worst_sin = max(worst_s, es), max(worst_sin, sin)
     return {"sigma_max_rel_err": worst_s, "v_subspace_sin_max": worst_sin, "queries": int(nq),
-            "vs": "FP64 oracle on the same rounded rows"}
+            "lengths": [int(np.min(te - ts + 1)), int(np.max(te - ts + 1))],
+            "vs": "FP64 oracle on the same rounded rows", "per_query": per}
 
 
-def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0):
+def plain_fp32_run(st, ts, te, k, budget_s=2.0):
+    """The batched form's own FP32 store, one zs_query call per query,
+    synchronised before the next: the same precision as the batch, no
+    batching, no graphs."""
+    import torch
+    lmax = int(np.max(te - ts + 1))
+    out = st.new_result(0, lmax - 1, k)
+    st.query(int(ts[0]), int(te[0]), out=out)
+    torch.cuda.synchronize()
+    nq, t0 = 0, time.perf_counter()
+    while nq < len(ts) and time.perf_counter() - t0 < budget_s:
+        st.query(int(ts[nq]), int(te[nq]), out=out)
+        torch.cuda.synchronize()
+        nq += 1
+    return {"form": "the same FP32 store, one zs_query call per query, synchronised", "queries": nq,
+            "queries_per_s": nq / (time.perf_counter() - t0)}
+
+
+def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0, warmup: float = 1.0):
     """Serving workload: compressed store of the serving shape, Poisson
     arrivals at rate_hz with lengths log-uniform 1e3..1e6, new blocks
-    appended at 1 block/ms on another stream while queries run."""
+    appended at 1 block/ms on another stream while queries run.  A first
+    server runs `warmup` seconds of arrivals (its statistics are dropped);
+    a fresh server then runs `seconds`, which are reported."""
     import torch
     import paper_1805_00754_gb300 as zs
     w = synthetic.WORKLOADS["serving_f32"]
     T, n, b, k = w.series.T, w.series.n, w.b, w.k
-    extra = int(seconds * 1000) + 16                      # blocks appended during the run
+    extra = int((seconds + warmup) * 1000) + 32            # blocks appended during both phases
     A = synthetic.rows(w.series, dtype=np.float32)
     app = synthetic.rows(synthetic.SeriesSpec(extra * b, n, w.series.s, w.series.noise, 0.0,
                                               w.series.seed + 1), dtype=np.float32)
@@ -582,62 +809,70 @@ def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0):
     st.append(torch.from_numpy(A).to(f"cuda:{local}"))
     app_dev = torch.from_numpy(app).to(f"cuda:{local}")
     torch.cuda.synchronize()
-    arrivals = synthetic.poisson_arrivals(rate_hz, seconds, seed=synthetic.SEED_BASE + 5)
-    ts, te = synthetic.queries(T, len(arrivals), w.lmin, w.lmax, seed=synthetic.SEED_BASE + 6)
     # results go to a ring arena (never read back); a slot is reused only after
     # its previous request completed
     arena_rows = 256 << 20
     arena = torch.empty((arena_rows, k), dtype=torch.float32, device=f"cuda:{local}")
     SV = torch.empty((4096, k), dtype=torch.float32, device=f"cuda:{local}")
     VV = torch.empty((4096, n, k), dtype=torch.float32, device=f"cuda:{local}")
-    sv = zs.Server(st, max_batch=512, max_inflight=3, queue_capacity=1 << 16, memory_budget=8 << 30)
     from paper_1805_00754_gb300 import zoomsvd
     import ctypes as C
     app_stream = torch.cuda.Stream(device=f"cuda:{local}")
-    stop = threading.Event()
+    lib = zoomsvd.lib()
+    state = {"appended": 0}
 
-    def appender():
-        i = 0
-        t0 = time.perf_counter()
-        while not stop.is_set() and i < extra:
-            st.append(app_dev[i * b:(i + 1) * b], stream=app_stream)
-            i += 1
-            nxt = t0 + i * 1e-3
-            d = nxt - time.perf_counter()
+    def phase(dur, seed):
+        sv = zs.Server(st, max_batch=512, max_inflight=3, queue_capacity=1 << 16, memory_budget=8 << 30)
+        arrivals = synthetic.poisson_arrivals(rate_hz, dur, seed=seed)
+        ts, te = synthetic.queries(T, len(arrivals), w.lmin, w.lmax, seed=seed + 1)
+        stop = threading.Event()
+
+        def appender():
+            t0 = time.perf_counter()
+            i = 0
+            while not stop.is_set() and state["appended"] < extra:
+                j = state["appended"]
+                st.append(app_dev[j * b:(j + 1) * b], stream=app_stream)
+                state["appended"] += 1
+                i += 1
+                d = t0 + i * 1e-3 - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+
+        th = threading.Thread(target=appender)
+        pending, off = [], 0
+        tick = C.c_uint64()
+        arena_p, sv_p, vv_p = arena.data_ptr(), SV.data_ptr(), VV.data_ptr()
+        t_start = time.perf_counter()
+        th.start()
+        for i, t_arr in enumerate(arrivals):
+            d = t_start + t_arr - time.perf_counter()
             if d > 0:
                 time.sleep(d)
-        return i
+            L = int(te[i] - ts[i] + 1)
+            if off + L > arena_rows:
+                off = 0
+            res = zoomsvd.Result(arena_p + off * k * 4, k, sv_p + (i % 4096) * k * 4,
+                                 vv_p + (i % 4096) * n * k * 4, k, 0)
+            off += L
+            if lib.zs_serve_submit(sv._h, int(ts[i]), int(te[i]), k, C.byref(res), C.byref(tick)) == 0:
+                pending.append(tick.value)
+        for t in pending:
+            sv.wait(t, 120_000)
+        stop.set()
+        th.join()
+        return sv.stop()
 
-    th = threading.Thread(target=appender)
-    pending = []
-    off = 0
-    t_start = time.perf_counter()
-    th.start()
-    lib = zoomsvd.lib()
-    tick = C.c_uint64()
-    arena_p, sv_p, vv_p = arena.data_ptr(), SV.data_ptr(), VV.data_ptr()
-    for i, t_arr in enumerate(arrivals):
-        d = t_start + t_arr - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        L = int(te[i] - ts[i] + 1)
-        if off + L > arena_rows:
-            off = 0
-        res = zoomsvd.Result(arena_p + off * k * 4, k, sv_p + (i % 4096) * k * 4,
-                             vv_p + (i % 4096) * n * k * 4, k, 0)
-        off += L
-        if lib.zs_serve_submit(sv._h, int(ts[i]), int(te[i]), k, C.byref(res), C.byref(tick)) == 0:
-            pending.append(tick.value)
-    for t in pending:
-        sv.wait(t, 120_000)
-    stop.set()
-    th.join()
-    stats = sv.stop()
+    if warmup > 0:
+        phase(warmup, synthetic.SEED_BASE + 15)
+    stats = phase(seconds, synthetic.SEED_BASE + 5)
+    status = st.status_counts(check=False)
     st.close()
-    return {"workload": "serving_f32", "offered_qps": rate_hz, "seconds": seconds,
+    return {"workload": "serving_f32", "offered_qps": rate_hz, "seconds": seconds, "warmup_s": warmup,
             "completed": stats["completed"], "rejected": stats["rejected"],
             "queries_per_s": stats["queries_per_s"], "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
-            "max_ms": stats["max_ms"], "mean_batch": stats["mean_batch"], "appends_per_s": 1000.0}
+            "max_ms": stats["max_ms"], "mean_batch": stats["mean_batch"], "appends_per_s": 1000.0,
+            "unconverged": [status[0], status[1]]}
 
 
 def main():
@@ -652,7 +887,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=6.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--skip-accuracy", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="skip the one-query-at-a-time FP64 GPU form")
     ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")

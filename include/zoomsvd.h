@@ -243,6 +243,20 @@ zs_status zs_query(zs_store* st, int64_t t_s, int64_t t_e, int32_t k_out,
 zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
                          int32_t k_out, const zs_result* results, void* stream);
 
+/* The same batch with U returned factored (Algorithm 2's last step, Eq. 9,
+ * left to the caller): results[q].S, .V and .rank are filled as by
+ * zs_query_batch (.U is not used and may be NULL), and U_{S:E} stays as
+ * diag(S:E) U_r in the form of one coefficient matrix per covered block.
+ * coef (device, factor type, coef_rows x k_out, row-major) receives, for
+ * query q with blocks S_q..E_q (S = t_s / b, E = t_e / b), the k x k_out
+ * matrices C_{q,S}..C_{q,E} stacked from row k * sum_{p<q} (E_p - S_p + 1):
+ * the answer's rows that fall in block i are the store's U_i rows for them
+ * (zs_store_export_block) times C_{q,i}.  ZS_EINVAL if coef_rows is smaller
+ * than k * sum_q (E_q - S_q + 1); otherwise as zs_query_batch.             */
+zs_status zs_query_batch_factored(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
+                                  int32_t k_out, const zs_result* results, void* coef, int64_t coef_rows,
+                                  void* stream);
+
 /* Similar-range search (Section 6, case study).  L = base_te - base_ts + 1;
  * the windows are the ranges [t, t + L - 1] with t = base_ts - j * stride
  * >= 0, j = 1 .. nwin, nwin = min(max_windows, base_ts / stride).  Each is

@@ -192,7 +192,9 @@ zs_status plan_queries(const zs_store& st, int64_t Trows, const int64_t* ts, con
 // Run one planned batch on `stream` with executor `x`.  Results go to the
 // buffers recorded in plans.
 zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan>& plans,
-                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream) {
+                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream, void* coef,
+                    int64_t coef_row0) {
+    const int lift = coef ? 0 : 1;
     const int nq = (int)plans.size();
     const int64_t nslab = prefix[nq];
     zs_status s = x.reserve(st, nq, nslab, kq);
@@ -237,6 +239,7 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.kq = kq;
     a.kout = kout;
     a.fp64_refine = (st.cfg.flags & ZS_FLAG_FP64_REFINE) ? 1 : 0;
+    a.lift = lift;
     a.M = x.M;
     a.m_rows = x.cap_slabs * st.cfg.k;
     a.G = x.G;
@@ -254,17 +257,18 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     for (const QPlan& P : plans) max_rows = std::max(max_rows, P.nslab * (int)st.cfg.k);
     // the first batch of a (k_q, k_out) shape runs eagerly (it also sets the
     // kernels' attributes); later ones replay a captured graph
-    const bool warm = (x.w_kq == kq && x.w_kout == kout);
+    const bool warm = (x.w_kq == kq && x.w_kout == kout && x.w_lift == lift);
     if (profiling_on() || !st.use_graphs || !warm) {
         x.w_kq = kq;
         x.w_kout = kout;
+        x.w_lift = lift;
         // eager: grids sized to this batch (the profiler brackets each launch)
         ZS_CU(cudaMemcpyAsync(x.d_blob, x.h_blob, bytes, cudaMemcpyHostToDevice, stream), "plan upload");
         QueryGrid g{nq, nslab, ntiles, max_rows};
         cudaError_t e = launch_query(a, st.fp64, g, st.cfg.flags, st.tune, st.num_sms, stream);
         if (e != cudaSuccess) return cuda_fail(e, "query kernels");
     } else {
-        if (!x.gexec || x.g_kq != kq || x.g_kout != kout) {
+        if (!x.gexec || x.g_kq != kq || x.g_kout != kout || x.g_lift != lift) {
             if (x.gexec) { cudaGraphExecDestroy(x.gexec); x.gexec = nullptr; }
             // capture the plan upload (whole buffer) and the kernels, with
             // grids sized to the executor's capacity
@@ -282,11 +286,23 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
             if (e != cudaSuccess) { x.gexec = nullptr; return cuda_fail(e, "graph instantiate"); }
             x.g_kq = kq;
             x.g_kout = kout;
+            x.g_lift = lift;
             x.g_launches = launch_count_total() - l0;
             note_launches(-x.g_launches);   // counted when replayed
         }
         ZS_CU(cudaGraphLaunch(x.gexec, stream), "graph launch");
         note_launches(x.g_launches);
+    }
+    if (coef) {
+        // the factored U: every slab's coefficients (stored U rows x C = the
+        // answer's rows in that block), k rows per slab, kout columns
+        const size_t ts = st.tsize;
+        char* dst = (char*)coef + ts * (size_t)coef_row0 * kout;
+        const int64_t rows = nslab * st.cfg.k;
+        ZS_CU(cudaMemcpy2DAsync(dst, ts * kout, x.C, ts * kq, ts * kq, rows, cudaMemcpyDeviceToDevice, stream),
+              "coefficient copy");
+        if (kout > kq)
+            ZS_CU(cudaMemset2DAsync(dst + ts * kq, ts * kout, 0, ts * (kout - kq), rows, stream), "coefficient pad");
     }
     ZS_CU(cudaEventRecord(x.done, stream), "event record");
     return ZS_OK;
@@ -793,7 +809,8 @@ extern "C" zs_status zs_store_export_block(const zs_store* st_, int64_t i, void*
 // ---------------------------------------------------------------------------
 namespace zs {
 zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, const int64_t* te, int nq, int kout,
-                             const zs_result* res, cudaStream_t stream, int64_t Trows) {
+                             const zs_result* res, cudaStream_t stream, int64_t Trows, void* coef,
+                             int64_t coef_rows) {
     const int kq = std::min<int>(kout, (int)st->cfg.n);
     const bool ref = (st->cfg.flags & ZS_FLAG_FP64_REFINE) && !st->fp64;
     if (!eig_plan((int)st->cfg.n, kq, st->tune.eig_m_extra, st->fp64, ref).ok)
@@ -803,9 +820,12 @@ zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, cons
     std::vector<int64_t> prefix;
     zs_status s = plan_queries(*st, Trows, ts, te, nq, kq, plans, prefix);
     if (s != ZS_OK) return s;
+    if (coef && prefix[nq] * st->cfg.k > coef_rows)
+        return fail(ZS_EINVAL, "coefficient buffer holds %lld rows; the batch needs %lld", (long long)coef_rows,
+                    (long long)(prefix[nq] * st->cfg.k));
     for (int q = 0; q < nq; ++q) {
         const zs_result& r = res[q];
-        if (!r.U || !r.S || !r.V || r.ldu < kout || r.ldv < kout)
+        if ((!coef && (!r.U || r.ldu < kout)) || !r.S || !r.V || r.ldv < kout)
             return fail(ZS_EINVAL, "query %d: bad result buffers", q);
         plans[q].U = r.U;
         plans[q].ldu = r.ldu;
@@ -845,7 +865,7 @@ zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, cons
             pre[q] = sub[q].slab0;
         }
         pre[q1 - q0] = sl;
-        if ((s = run_batch(*st, x, Trows, sub, pre, kq, kout, stream)) != ZS_OK) return s;
+        if ((s = run_batch(*st, x, Trows, sub, pre, kq, kout, stream, coef, base * st->cfg.k)) != ZS_OK) return s;
         q0 = q1;
     }
     return ZS_OK;
@@ -860,6 +880,17 @@ extern "C" zs_status zs_query_batch(zs_store* st, const int64_t* ts, const int64
     std::lock_guard<std::mutex> lk(st->mu);
     DeviceGuard g(st->cfg.device);
     return query_batch_locked(st, st->qx, ts, te, nq, k_out, results, (cudaStream_t)stream, st->T);
+}
+
+extern "C" zs_status zs_query_batch_factored(zs_store* st, const int64_t* ts, const int64_t* te, int32_t nq,
+                                             int32_t k_out, const zs_result* results, void* coef, int64_t coef_rows,
+                                             void* stream) {
+    if (!st || !ts || !te || !results || !coef || nq < 0 || coef_rows < 0) return fail(ZS_EINVAL, "null argument");
+    if (nq == 0) return ZS_OK;
+    if (k_out < 1 || k_out > 64) return fail(ZS_EINVAL, "k_out %d not in 1..64", k_out);
+    std::lock_guard<std::mutex> lk(st->mu);
+    DeviceGuard g(st->cfg.device);
+    return query_batch_locked(st, st->qx, ts, te, nq, k_out, results, (cudaStream_t)stream, st->T, coef, coef_rows);
 }
 
 // ---------------------------------------------------------------------------

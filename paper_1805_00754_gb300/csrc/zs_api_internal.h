@@ -32,8 +32,8 @@ struct QueryExec {
     // executor's capacity, replayed for every batch that fits it
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int g_kq = -1, g_kout = -1;
-    int w_kq = -1, w_kout = -1;      // shape of the last eager batch
+    int g_kq = -1, g_kout = -1, g_lift = -1;
+    int w_kq = -1, w_kout = -1, w_lift = -1;   // shape of the last eager batch
     int64_t g_launches = 0;
     ~QueryExec();
     void release();
@@ -45,10 +45,14 @@ zs_status fail(zs_status s, const char* fmt, ...);
 zs_status cuda_fail(cudaError_t e, const char* what);
 zs_status plan_queries(const zs_store& st, int64_t Trows, const int64_t* ts, const int64_t* te, int nq, int kq,
                        std::vector<QPlan>& plans, std::vector<int64_t>& prefix);
+// coef != null: U stays factored; the batch's per-slab coefficients (nslab
+// * k rows of kout) are copied to coef (device, factor type) from row coef_row0
 zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan>& plans,
-                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream);
+                    std::vector<int64_t>& prefix, int kq, int kout, cudaStream_t stream, void* coef = nullptr,
+                    int64_t coef_row0 = 0);
 zs_status query_batch_locked(zs_store* st, QueryExec& x, const int64_t* ts, const int64_t* te, int nq, int kout,
-                             const zs_result* res, cudaStream_t stream, int64_t Trows);
+                             const zs_result* res, cudaStream_t stream, int64_t Trows, void* coef = nullptr,
+                             int64_t coef_rows = 0);
 
 }  // namespace zs
 

@@ -100,6 +100,7 @@ struct QueryArgs {
     int32_t kq;                   // eigenpairs computed per query (= min(k_out, n))
     int32_t kout;
     int32_t fp64_refine;
+    int32_t lift;     // 1: materialise U (the lift); 0: leave U factored as the per-slab coefficients C
     // scratch
     void* M;          // nslab_total * k * n     stacked Sigma_i V_i^T
     int64_t m_rows;   // rows allocated behind M (slab capacity x k)

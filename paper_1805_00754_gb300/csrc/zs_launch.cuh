@@ -388,10 +388,8 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
                 k_bfix<<<std::min(2 * max_nq, pers), 256, sm, st>>>(a);
                 ZS_TRY(cudaGetLastError());
             }
-            {
-                ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
-            }
-            note_launches(3);
+            if (a.lift) ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
+            note_launches(a.lift ? 3 : 2);
             return cudaSuccess;
         }
     }
@@ -425,8 +423,8 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
         k_ur<T><<<std::min(max_nq, pers), 256, sm, st>>>(a);
         ZS_TRY(cudaGetLastError());
     }
-    ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
-    note_launches(5);
+    if (a.lift) ZS_TRY(launch_lift<T>(a, max_slabs, num_sms, st));
+    note_launches(a.lift ? 5 : 4);
     return cudaSuccess;
 }
 

@@ -74,6 +74,8 @@ SIGNATURES = {
     "zs_noalloc_status": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "zs_query": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(Result), C.c_void_p]),
     "zs_store_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "zs_query_batch_factored": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32,
+                                          C.c_int32, C.POINTER(Result), C.c_void_p, C.c_int64, C.c_void_p]),
     "zs_query_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32, C.c_int32,
                                  C.POINTER(Result), C.c_void_p]),
     "zs_serve_start": (C.c_int, [C.c_void_p, C.POINTER(ServeConfig), C.POINTER(C.c_void_p)]),
@@ -259,6 +261,19 @@ class Store:
                                        _stream_ptr(stream)))
         return [(int(starts[j]), float(cos[j])) for j in range(nw.value)]
 
+    def query_batch_factored(self, ts, te, k_out: int | None = None, out: "FactoredBatch | None" = None,
+                             stream=None):
+        """Batch with U left factored (zs_query_batch_factored)."""
+        k_out = self.k if k_out is None else k_out
+        ts = np.ascontiguousarray(ts, dtype=np.int64)
+        te = np.ascontiguousarray(te, dtype=np.int64)
+        out = out or FactoredBatch(self, ts, te, k_out)
+        res = (Result * len(ts))(*out.results())
+        _check(lib().zs_query_batch_factored(self._h, ts.ctypes.data_as(C.POINTER(C.c_int64)),
+                                             te.ctypes.data_as(C.POINTER(C.c_int64)), len(ts), k_out, res,
+                                             out.coef.data_ptr(), out.coef.shape[0], _stream_ptr(stream)))
+        return out
+
     def query_batch(self, ts, te, k_out: int | None = None, outs=None, stream=None):
         k_out = self.k if k_out is None else k_out
         ts = np.ascontiguousarray(ts, dtype=np.int64)
@@ -271,6 +286,32 @@ class Store:
                                     te.ctypes.data_as(C.POINTER(C.c_int64)), nq, k_out, res,
                                     _stream_ptr(stream)))
         return outs
+
+
+class FactoredBatch:
+    """Device tensors of a batch answered with U factored: S (nq x k_out),
+    V (nq x n x k_out), rank (nq), and coef (sum of the queries' covered
+    blocks x k rows, k_out columns); offsets[q] is query q's first
+    coefficient row."""
+
+    def __init__(self, store, ts, te, k_out):
+        b, k = store.b, store.k
+        nblk = te // b - ts // b + 1
+        self.offsets = np.concatenate([[0], np.cumsum(nblk)])[:-1] * k
+        self.rows = int(np.sum(nblk)) * k
+        dev, dt = store.device, store.fdtype
+        nq = len(ts)
+        self.S = torch.empty((nq, k_out), dtype=dt, device=dev)
+        self.V = torch.empty((nq, store.n, k_out), dtype=dt, device=dev)
+        self.rank = torch.zeros((nq,), dtype=torch.int32, device=dev)
+        self.coef = torch.empty((max(self.rows, 1), k_out), dtype=dt, device=dev)
+        self.k_out = k_out
+
+    def results(self):
+        es = self.S.element_size()
+        return [Result(0, self.k_out, self.S.data_ptr() + q * self.k_out * es,
+                       self.V.data_ptr() + q * self.V.shape[1] * self.k_out * es, self.k_out,
+                       self.rank.data_ptr() + 4 * q) for q in range(self.S.shape[0])]
 
 
 class Server:

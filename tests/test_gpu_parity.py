@@ -295,3 +295,39 @@ def test_serving_results_equal_alone():
         alone = st.query(int(a), int(z))
         torch.cuda.synchronize()
         assert torch.equal(alone.S, out.S) and torch.equal(alone.U, out.U) and torch.equal(alone.V, out.V)
+
+
+def test_factored_batch_matches_materialised():
+    """zs_query_batch_factored: S, V and rank equal the materialised batch's
+    bit for bit, and the stored U_i rows times each block's coefficients
+    (Eq. 9, composed here in FP64) give its U to FP32 rounding."""
+    w, A = _reduced("ragged_batch_f32", 10, 304)
+    st, exact = gpu_store(A, w.b, w.k, "f32")
+    T = A.shape[0]
+    ts, te = synthetic.queries(T, 20, 500, 15_000, seed=41)
+    mat = st.query_batch(ts, te)
+    fac = st.query_batch_factored(ts, te)
+    torch.cuda.synchronize()
+    blocks = {}
+    for q in range(len(ts)):
+        assert torch.equal(mat[q].S, fac.S[q]) and torch.equal(mat[q].V, fac.V[q])
+        assert torch.equal(mat[q].rank[0], fac.rank[q])
+        a, z = int(ts[q]), int(te[q])
+        parts = []
+        for t, i in enumerate(range(a // w.b, z // w.b + 1)):
+            if i not in blocks:
+                blocks[i] = _to_np(st.export_block(i)[0])
+            lo, hi = max(a, i * w.b), min(z, (i + 1) * w.b - 1)
+            C = _to_np(fac.coef[fac.offsets[q] + t * w.k: fac.offsets[q] + (t + 1) * w.k])
+            parts.append(blocks[i][lo - i * w.b: hi - i * w.b + 1] @ C)
+        U = np.vstack(parts)
+        Um = _to_np(mat[q].U)
+        assert U.shape == Um.shape
+        assert np.max(np.abs(U - Um)) <= 1e-5 * max(1.0, np.max(np.abs(Um))), f"query {q}"
+    from paper_1805_00754_gb300 import ZsError
+    with pytest.raises(ZsError) as e:
+        from paper_1805_00754_gb300.zoomsvd import FactoredBatch
+        small = FactoredBatch(st, ts, te, w.k)
+        small.coef = small.coef[:w.k]             # too few rows
+        st.query_batch_factored(ts, te, out=small)
+    assert e.value.status == 1
