@@ -672,6 +672,78 @@ def run_sweep_b(args, w):
                       "dtype": w.dtype, "lengths": list(SWEEP_LEN), "points": points}))
 
 
+SWEEP_XI = (0.95, 0.98, 0.99)
+
+
+def run_sweep_xi(args, w, kcap=32, nq_err=8):
+    """Energy-rule sweep (Eq. 1; Fig. 6 of Section 5.4 on the synthetic
+    workload): for xi = 0.95, 0.98, 0.99 (ranks capped at kcap) and for the
+    workload's fixed rank, the per-block ranks k_i, the space the store keeps
+    (Theorem 3: sum k_i (b + n + 1) values against T n raw values), the stored
+    blocks' relative squared reconstruction error, the same error of query
+    results against the raw rows (nq_err ranges of the bench's lengths), the
+    compression time and queries/s of the bench's batch.  One JSON line."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1805_00754_gb300 as zs
+    T, n, b = w.series.T, w.series.n, w.b
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    A = _input_rows(w)
+    rows_dev = torch.from_numpy(A).cuda()
+    A64 = synthetic.bf16_bits_to_f64(A.view(np.uint16)) if w.dtype == "bf16" else None
+    stream = torch.cuda.current_stream()
+    ts, te = synthetic.queries(T, w.nq or 256, w.lmin or 1_000, w.lmax or T, seed=synthetic.SEED_BASE + 99)
+    qa, qz = synthetic.queries(T, nq_err, w.lmin or 1_000, w.lmax or T, seed=synthetic.SEED_BASE + 97)
+    points = []
+    for xi in (None,) + SWEEP_XI:
+        k = w.k if xi is None else kcap
+        st = zs.Store(n=n, b=b, k=k, dtype=w.dtype, capacity_rows=T, xi=xi, fp64_refine=(w.dtype == "bf16"))
+        st.append(rows_dev)
+        torch.cuda.synchronize()
+        st.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.append(rows_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        comp_ms = e0.elapsed_time(e1)
+        ranks, kept, en = st.block_stats()
+        if xi is None:
+            en = np.array([np.sum((A64 if A64 is not None else A)[i * b:(i + 1) * b].astype(np.float64) ** 2)
+                           for i in range(len(ranks))])
+        kq = w.k          # queries ask for the workload's rank whatever the blocks keep
+        outs = [st.new_result(int(a), int(z), kq) for a, z in zip(ts, te)]
+        st.query_batch(ts, te, kq, outs)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st.query_batch(ts, te, kq, outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        qps = len(ts) / (e0.elapsed_time(e1) / 1e3)
+        del outs
+        qerr = []
+        for a, z in zip(qa, qz):
+            o = st.query(int(a), int(z), kq)
+            torch.cuda.synchronize()
+            U, S, V = (x.cpu().numpy().astype(np.float64) for x in (o.U, o.S, o.V))
+            X = (A64 if A64 is not None else A)[int(a):int(z) + 1].astype(np.float64)
+            R = X - (U * S[None, :]) @ V.T
+            qerr.append(float(np.sum(R * R) / np.sum(X * X)))
+        status = st.status_counts(check=False)
+        points.append({"xi": xi, "k_cap": k, "k_i_min": int(ranks.min()), "k_i_mean": float(ranks.mean()),
+                       "k_i_max": int(ranks.max()), "space_values": int(np.sum(ranks) * (b + n + 1)),
+                       "space_vs_raw": float(np.sum(ranks) * (b + n + 1) / (T * n)),
+                       "store_recon_err": float(1.0 - np.sum(kept) / np.sum(en)),
+                       "query_recon_err_mean": float(np.mean(qerr)), "query_recon_err_max": float(np.max(qerr)),
+                       "compress_ms": comp_ms, "compress_gbs": T * n * itemsize / comp_ms / 1e6,
+                       "queries_per_s": qps, "unconverged": [status[0], status[1]]})
+        st.close()
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "xi", "workload": w.name, "T": T, "n": n, "b": b, "dtype": w.dtype,
+                      "query_lengths": [int(np.min(te - ts + 1)), int(np.max(te - ts + 1))], "points": points}))
+
+
 def plain_fp64_run(w, A, ts, te, local, budget_s=4.0, acc_queries=3):
     """The same range-SVD method as a plain FP64 GPU program, one query at a
     time: an FP64 store of the same rows (FP64 CUDA-core kernels throughout),
@@ -894,12 +966,16 @@ def main():
     ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")
     ap.add_argument("--sweep-b", action="store_true",
                     help="block-size sweep (compression time, space, queries/s at 1e3/1e4/1e5 rows)")
+    ap.add_argument("--sweep-xi", action="store_true",
+                    help="energy-rule sweep xi = 0.95/0.98/0.99 (ranks, space, reconstruction error, rates)")
     args = ap.parse_args()
     w = synthetic.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
     elif args.sweep_b:
         run_sweep_b(args, w)
+    elif args.sweep_xi:
+        run_sweep_xi(args, w)
     else:
         run_gpu(args, w)
 

@@ -142,6 +142,18 @@ zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
  * per-block scratch (8 bytes per block of capacity) cannot be allocated.    */
 zs_status zs_store_set_xi(zs_store* st, double xi);
 
+/* Per-block ranks and energies (Eq. 1; Theorem 3; the reconstruction error
+ * of Section 5.4).  Synchronises the device.  For blocks 0 .. nblocks-1
+ * (host arrays, any may be NULL): ranks[i] = k_i, the energy rule's rank in
+ * xi mode (its columns are the nonzero ones) or min(k, rows_i, n) at fixed
+ * rank; kept[i] = sum_{j < k_i} sigma_ij^2, the energy the block keeps;
+ * energy[i] = ||X_i||_F^2 as measured when the block was compressed in xi
+ * mode, else -1.  The paper's space for the store is
+ * sum_i k_i (b + n + 1) values, and 1 - sum kept / sum energy is the
+ * stored blocks' relative squared reconstruction error (Eckart-Young).
+ * ZS_ENOTFOUND if nblocks exceeds the store's blocks.                      */
+zs_status zs_store_block_stats(const zs_store* st, int64_t nblocks, int32_t* ranks, double* kept, double* energy);
+
 /* Device fault word of the store (failure detection): 1 once a kernel of
  * this store gave up a bounded wait on the device (the tensor-core
  * projection waits on its MMA completions with an iteration limit, then

@@ -464,6 +464,7 @@ extern "C" void zs_store_destroy(zs_store* st) {
     f(st->U); f(st->sig); f(st->vt); f(st->w); if (st->d_fault) cudaFree(st->d_fault); f(st->tail); f(st->gscr); f(st->stage[0]); f(st->stage[1]); f(st->ews);
     f(st->qb); f(st->ys); f(st->aux);
     if (st->d_energy) cudaFree(st->d_energy);
+    if (st->d_rank) cudaFree(st->d_rank);
     for (int i = 0; i < 2; ++i) {
         if (st->stage_free[i]) cudaEventDestroy(st->stage_free[i]);
         if (st->stage_full[i]) cudaEventDestroy(st->stage_full[i]);
@@ -526,6 +527,7 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
             ch.refined = st->d_fault + 3;
             ch.xi = st->xi;
             ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
+            ch.kxi = st->d_rank ? st->d_rank + ch.slot0 : nullptr;
             ch.ews = st->ews;
             ch.ews_ctas = st->ews_ctas;
             ch.qb = (char*)st->qb + (size_t)r * sub * 4 * tc_qb_floats((int)m, (int)c.n);
@@ -564,6 +566,7 @@ static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64
         ch.refined = st->d_fault + 3;
         ch.xi = st->xi;
         ch.energy = st->d_energy ? st->d_energy + ch.slot0 : nullptr;
+        ch.kxi = st->d_rank ? st->d_rank + ch.slot0 : nullptr;
         ch.ews = st->ews;
         ch.ews_ctas = st->ews_ctas;
         ch.qb = st->qb;
@@ -734,11 +737,14 @@ extern "C" zs_status zs_store_set_xi(zs_store* st, double xi) {
     std::lock_guard<std::mutex> lk(st->mu);
     DeviceGuard g(st->cfg.device);
     if (xi > 0.0 && !st->d_energy) {
-        const size_t bytes = sizeof(double) * (size_t)std::max<int64_t>(st->cap_blocks, 1);
-        if (cudaMalloc((void**)&st->d_energy, bytes) != cudaSuccess) {
+        const size_t nb = (size_t)std::max<int64_t>(st->cap_blocks, 1);
+        if (cudaMalloc((void**)&st->d_energy, sizeof(double) * nb) != cudaSuccess ||
+            cudaMalloc((void**)&st->d_rank, sizeof(int) * nb) != cudaSuccess) {
             cudaGetLastError();
+            if (st->d_energy) cudaFree(st->d_energy);
             st->d_energy = nullptr;
-            return fail(ZS_ENOMEM, "block energies (%zu bytes)", bytes);
+            st->d_rank = nullptr;
+            return fail(ZS_ENOMEM, "block energies and ranks (%zu bytes)", 12 * nb);
         }
     }
     st->xi = xi;
@@ -769,6 +775,48 @@ extern "C" zs_status zs_store_status(const zs_store* st, int64_t* unconverged_bl
     if (v[1] || v[2])
         return fail(ZS_ENOCONV, "%d block(s) and %d query result(s) did not pass the accuracy test within the pass cap",
                     v[1], v[2]);
+    return ZS_OK;
+}
+
+extern "C" zs_status zs_store_block_stats(const zs_store* st_, int64_t nblocks, int32_t* ranks, double* kept,
+                                         double* energy) {
+    zs_store* st = const_cast<zs_store*>(st_);
+    if (!st || nblocks < 0) return fail(ZS_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(st->mu);
+    const int64_t T = st->T, b = st->cfg.b, n = st->cfg.n, k = st->cfg.k;
+    const int64_t nb = (T + b - 1) / b;
+    if (nblocks > nb) return fail(ZS_ENOTFOUND, "%lld blocks asked for, the store holds %lld", (long long)nblocks,
+                                  (long long)nb);
+    if (nblocks == 0) return ZS_OK;
+    DeviceGuard g(st->cfg.device);
+    ZS_CU(cudaDeviceSynchronize(), "stats wait");
+    std::vector<double> sig((size_t)nblocks * k);
+    if (st->fp64) {
+        ZS_CU(cudaMemcpy(sig.data(), st->sig, 8 * sig.size(), cudaMemcpyDeviceToHost), "sigma copy");
+    } else {
+        std::vector<float> f(sig.size());
+        ZS_CU(cudaMemcpy(f.data(), st->sig, 4 * f.size(), cudaMemcpyDeviceToHost), "sigma copy");
+        for (size_t i = 0; i < f.size(); ++i) sig[i] = f[i];
+    }
+    std::vector<double> en;
+    if (energy && st->xi > 0.0 && st->d_energy) {
+        en.resize(nblocks);
+        ZS_CU(cudaMemcpy(en.data(), st->d_energy, 8 * nblocks, cudaMemcpyDeviceToHost), "energy copy");
+    }
+    for (int64_t i = 0; i < nblocks; ++i) {
+        const int64_t rows = std::min(b, T - i * b);
+        const int64_t cap = std::min(k, std::min(rows, n));
+        int32_t ki = (int32_t)cap;
+        double kk = 0.0;
+        if (st->xi > 0.0) {      // the energy rule's rank: the columns it kept are the nonzero ones
+            ki = 0;
+            for (int64_t j = 0; j < cap; ++j) ki += sig[i * k + j] > 0.0;
+        }
+        for (int64_t j = 0; j < cap; ++j) kk += sig[i * k + j] * sig[i * k + j];
+        if (ranks) ranks[i] = ki;
+        if (kept) kept[i] = kk;
+        if (energy) energy[i] = en.empty() ? -1.0 : en[i];
+    }
     return ZS_OK;
 }
 

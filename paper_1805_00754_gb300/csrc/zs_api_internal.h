@@ -71,6 +71,7 @@ struct zs_store {
     int* d_fault = nullptr;        // device fault word (bounded waits that gave up)
     double xi = 0.0;               // > 0: energy rule (Eq. 1) picks each block's rank <= k
     double* d_energy = nullptr;    // xi > 0: per slot ||X_i||_F^2 (cap_blocks doubles)
+    int* d_rank = nullptr;         // xi > 0: per slot rank k_i as the accuracy test decided it
     void* tail = nullptr;          // b x n raw rows of the open block
     void* gscr = nullptr;          // gchunk x n x n Gram scratch
     void* ews = nullptr;           // eigen-core workspace

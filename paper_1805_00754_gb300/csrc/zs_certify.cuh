@@ -308,7 +308,13 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
         if (tid == 0) {
             for (int j = 0; j < kw; ++j) s_rho[j] = sqrtf(s_rho[j]);
             const float sm = sqrtf(fmaxf(sc.thm[(size_t)item * m + m - 1], 0.f));
-            if (!cert_pass(s_sig, s_rho, kc, sm)) {
+            int kt = kc;
+            if (sc.kxi) {              // only the pairs the energy rule keeps are tested
+                const int ki = xi_rank_of(s_sig, kw, sc.energy[item], sc.xi);
+                sc.kxi[item] = ki;
+                kt = min(kc, ki);
+            }
+            if (!cert_pass(s_sig, s_rho, kt, sm)) {
                 const int p = atomicAdd(sc.list, 1);
                 sc.list[2 + p] = item;
             }
@@ -531,7 +537,13 @@ __global__ void __launch_bounds__(kRefineThreads, 1) k_refine(Src src, TcScratch
             }
             __syncthreads();
             if (tid == 0) {
-                const bool ok = cert_pass(s_sig, s_rho, kc, sqrtf(s_th[MR - 1]));
+                int kt = kc;
+                if (sc.kxi) {          // the energy rule's rank from the refined values
+                    const int ki = xi_rank_of(s_sig, kw, sc.energy[item], sc.xi);
+                    sc.kxi[item] = ki;
+                    kt = min(kc, ki);
+                }
+                const bool ok = cert_pass(s_sig, s_rho, kt, sqrtf(s_th[MR - 1]));
                 s_done = ok ? 1 : (pass >= kRefineMaxPasses ? 2 : 0);
             }
             __syncthreads();

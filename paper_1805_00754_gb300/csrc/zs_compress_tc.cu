@@ -19,6 +19,9 @@ static cudaError_t compress_tc(const CompressChunk& c, const Tuning& tu, int num
     sc.fault = c.fault;
     sc.noconv = c.noconv;
     sc.refined = c.refined;
+    sc.xi = c.xi;
+    sc.energy = c.energy;
+    sc.kxi = (c.xi > 0.0 && c.energy) ? c.kxi : nullptr;
     SrcCompress src{c};
     const bool aligned = (reinterpret_cast<uintptr_t>(c.A) % 16 == 0) && (c.lda % 4 == 0);
     return tc_core<SrcCompress, Tin, REF, false>(src, sc, c.n, c.k, c.nblk,

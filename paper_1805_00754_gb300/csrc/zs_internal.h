@@ -45,6 +45,7 @@ struct CompressChunk {
     int* refined;     // device count of blocks that needed refinement (or null)
     double xi;        // > 0: energy rule of Eq. 1 per block (rank k_i <= k), else fixed k
     double* energy;   // xi > 0: nblk doubles of scratch (each block's squared Frobenius norm)
+    int* kxi;         // xi > 0: nblk ints, each block's rank k_i as the accuracy test decided it
 };
 
 // Per-query plan of a batch (host-computed, then copied to the device).

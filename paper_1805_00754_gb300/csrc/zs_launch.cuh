@@ -377,6 +377,9 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             sc.fault = a.fault;
             sc.noconv = a.noconv;
             sc.refined = a.refined;
+            sc.xi = 0.0;
+            sc.energy = nullptr;
+            sc.kxi = nullptr;
             SrcQuery src{a};
             // stacked rows (M and the store's Sigma V^T) are 16-byte aligned when n % 4 == 0
             ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,

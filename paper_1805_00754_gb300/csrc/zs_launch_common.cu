@@ -199,22 +199,7 @@ __global__ void __launch_bounds__(256) k_xi_truncate(CompressChunk c) {
     const int64_t slot = (int64_t)c.slot0 + j;
     const int k = c.k, n = c.n;
     T* sig = (T*)c.sig + slot * k;
-    if (threadIdx.x == 0) {
-        const double e = c.energy[j], goal = c.xi * e;
-        int ki = 0;
-        if (e > 0.0) {
-            ki = k;
-            double cum = 0.0;
-            for (int l = 0; l < k; ++l) {
-                cum += (double)sig[l] * (double)sig[l];
-                if (cum >= goal) {
-                    ki = l + 1;
-                    break;
-                }
-            }
-        }
-        ki_s = ki;
-    }
+    if (threadIdx.x == 0) ki_s = c.kxi ? c.kxi[j] : xi_rank_of(sig, k, c.energy[j], c.xi);
     __syncthreads();
     const int ki = ki_s;
     if (ki >= k) return;
@@ -236,19 +221,26 @@ __global__ void __launch_bounds__(256) k_xi_truncate(CompressChunk c) {
 
 cudaError_t launch_compress(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,
                             cudaStream_t st) {
-    cudaError_t e = use_tc_path(fp64, c.n, flags) ? launch_compress_tc(c, flags, tu, num_sms, st)
-                                                   : launch_compress_simt(c, fp64, flags, tu, num_sms, st);
-    if (e != cudaSuccess || !(c.xi > 0.0) || !c.energy || c.nblk < 1) return e;
-    {
+    const bool xi = c.xi > 0.0 && c.energy && c.nblk >= 1;
+    const bool tc = use_tc_path(fp64, c.n, flags);
+    cudaError_t e;
+    if (xi) {
+        // the blocks' energies first: the tensor path's accuracy test applies
+        // the energy rule and tests only the ranks it keeps
         prof::Scope ps("xi_energy", st);
         if (c.in_kind == IN_F64) k_block_energy<double><<<c.nblk, 256, 0, st>>>(c);
         else if (c.in_kind == IN_BF16) k_block_energy<__nv_bfloat16><<<c.nblk, 256, 0, st>>>(c);
         else k_block_energy<float><<<c.nblk, 256, 0, st>>>(c);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    e = tc ? launch_compress_tc(c, flags, tu, num_sms, st) : launch_compress_simt(c, fp64, flags, tu, num_sms, st);
+    if (e != cudaSuccess || !xi) return e;
+    // the tensor path recorded each block's rank k_i; the CUDA-core path decides it here
+    CompressChunk ct = c;
+    if (!tc || !c.kxi) ct.kxi = nullptr;
     prof::Scope ps("xi_truncate", st);
-    if (fp64) k_xi_truncate<double><<<c.nblk, 256, 0, st>>>(c);
-    else k_xi_truncate<float><<<c.nblk, 256, 0, st>>>(c);
+    if (fp64) k_xi_truncate<double><<<c.nblk, 256, 0, st>>>(ct);
+    else k_xi_truncate<float><<<c.nblk, 256, 0, st>>>(ct);
     return cudaGetLastError();
 }
 

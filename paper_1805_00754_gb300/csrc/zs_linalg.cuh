@@ -25,6 +25,21 @@
 
 namespace zs {
 
+// Energy rule (Eq. 1): the smallest rank whose leading singular values
+// (sig, descending, k of them) hold a fraction >= xi of the energy e; k if
+// they never do, 0 for an empty block.  FP64 sums in a fixed order.
+template <typename T>
+__device__ __forceinline__ int xi_rank_of(const T* sig, int k, double e, double xi) {
+    if (!(e > 0.0)) return 0;
+    const double goal = xi * e;
+    double cum = 0.0;
+    for (int l = 0; l < k; ++l) {
+        cum += (double)sig[l] * (double)sig[l];
+        if (cum >= goal) return l + 1;
+    }
+    return k;
+}
+
 template <typename T> __device__ __forceinline__ T eps_of();
 template <> __device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
 template <> __device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }

@@ -154,6 +154,9 @@ struct TcScratch {
     int* list;              // 2 + items ints: count, work counter, then the items that failed the accuracy test
     int* noconv;            // incremented per item whose refinement stopped at its pass cap (or null)
     int* refined;           // incremented per item refined (or null)
+    double xi;              // storage phase, xi > 0: energy rule (Eq. 1); only ranks < k_i are tested
+    const double* energy;   // xi > 0: each item's squared Frobenius norm
+    int* kxi;               // xi > 0: each item's rank k_i, recorded for the truncation
     int* fault;             // set to 1 by a kernel whose bounded wait gave up (or null)
 };
 

@@ -64,6 +64,8 @@ SIGNATURES = {
     "zs_store_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
     "zs_store_set_xi": (C.c_int, [C.c_void_p, C.c_double]),
+    "zs_store_block_stats": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
     "zs_similar_ranges": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_int32),
                                     C.c_void_p]),
@@ -226,6 +228,18 @@ class Store:
         if check or st not in (0, 5, 10):
             _check(st)
         return tuple(x.value for x in v)
+
+    def block_stats(self):
+        """(ranks k_i, kept energies, block energies or -1) of every block,
+        as numpy arrays (zs_store_block_stats)."""
+        nb = self.info()[1]
+        r = np.zeros(nb, dtype=np.int32)
+        kept = np.zeros(nb)
+        en = np.zeros(nb)
+        _check(lib().zs_store_block_stats(self._h, nb, r.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          kept.ctypes.data_as(C.POINTER(C.c_double)),
+                                          en.ctypes.data_as(C.POINTER(C.c_double))))
+        return r, kept, en
 
     def export_block(self, i: int, stream=None):
         U = torch.empty((self.b, self.k), dtype=self.fdtype, device=self.device)

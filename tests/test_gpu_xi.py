@@ -86,6 +86,47 @@ def test_xi_f32_tensor_path_ragged():
     assert st.fault() == 0
 
 
+def _check_stats(st, ost, exact, b, rtol):
+    """zs_store_block_stats against the oracle's compress(..., xi): per-block
+    ranks k_i (Eq. 1; they fix the paper's space sum k_i (b + n + 1),
+    Theorem 3), kept energy, the block energy ||X_i||_F^2 and the stored
+    blocks' relative reconstruction error (Section 5.4), which Eckart-Young
+    fixes."""
+    ranks, kept, en = st.block_stats()
+    nb = len(ost.s)
+    assert ranks.shape == (nb,)
+    T, n = exact.shape
+    want_r = np.array([np.count_nonzero(ost.s[i]) for i in range(nb)])
+    np.testing.assert_array_equal(ranks, want_r)
+    want_e = np.array([np.sum(exact[i * b:min((i + 1) * b, T)] ** 2) for i in range(nb)])
+    np.testing.assert_allclose(en, want_e, rtol=1e-12)
+    # sigma to rtol: the kept energy (a sum of squares) to 2 rtol
+    np.testing.assert_allclose(kept, [np.sum(ost.s[i] ** 2) for i in range(nb)], rtol=2 * rtol)
+    err_gpu = 1.0 - np.sum(kept) / np.sum(en)
+    err_ref = sum(np.sum((exact[i * b:min((i + 1) * b, T)] - (ost.U[i] * ost.s[i]) @ ost.Vt[i]) ** 2)
+                  for i in range(nb)) / np.sum(want_e)
+    assert abs(err_gpu - err_ref) <= max(1e-9, 50 * rtol * err_ref), (err_gpu, err_ref)
+    return ranks
+
+
+def test_xi_block_stats_and_reconstruction_error():
+    """Per-block ranks, energies, space and reconstruction error of xi stores
+    (FP64 plain workload, FP32 ragged tensor path) against the oracle."""
+    w = synthetic.WORKLOADS["plain_f64"]
+    A = synthetic.rows(w.series)
+    st, exact = _xi_store(A, w.b, w.k, "f64", 0.9)
+    _check_stats(st, oracle.compress(exact, w.b, w.k, xi=0.9), exact, w.b, 1e-10)
+    w = synthetic.WORKLOADS["ragged_batch_f32"]
+    A = synthetic.rows(w.series, 0, 8 * w.b + 304)
+    st, exact = _xi_store(A, w.b, w.k, "f32", 0.8)
+    r = _check_stats(st, oracle.compress(exact, w.b, w.k, xi=0.8), exact, w.b, 1e-4)
+    assert len(set(r.tolist())) > 1
+    # fixed rank: k_i = min(k, rows_i, n), energies not measured
+    st2, _ = _xi_store(A, w.b, w.k, "f32", None)
+    r2, kept2, en2 = st2.block_stats()
+    assert np.all(r2 == w.k) and np.all(en2 == -1.0) and np.all(kept2 > 0)
+
+
 def test_xi_errors_and_reset_to_fixed():
     from paper_1805_00754_gb300 import Store, ZsError
     st = Store(n=16, b=64, k=4, dtype="f32", capacity_rows=256)
