@@ -175,6 +175,24 @@ def compress_block_incremental(Ab: np.ndarray, k: int):
     return truncate(U, s, Vt, k)
 
 
+def compress_block_rowwise(Ab: np.ndarray, k: int, discarded: list | None = None):
+    """Algorithm 1 as printed, for one block: every arriving row updates the
+    block's rank-k SVD by Eq. 2-3 (SVD of [diag(s) Vt; a] and U <- blockdiag(U,
+    1) U~) and the result is truncated back to rank k after every row, so the
+    state never holds more than k triplets (the cost of Theorem 1).  Unlike
+    compress_block_incremental this is not the block's exact SVD once the
+    block's rank exceeds k.  ``discarded`` (if a list) receives the singular
+    value dropped at each row (0 while nothing is dropped)."""
+    Ab = np.asarray(Ab, dtype=np.float64)
+    U, s, Vt = truncate(*svd(Ab[:1]), k)
+    for t in range(1, Ab.shape[0]):
+        U, s, Vt = incremental_svd(U, s, Vt, Ab[t])
+        if discarded is not None:
+            discarded.append(float(s[k]) if s.size > k else 0.0)
+        U, s, Vt = truncate(U, s, Vt, k)
+    return U, s, Vt
+
+
 def compress_block_xi(Ab: np.ndarray, k: int, xi: float):
     """Stored factors of one block under the energy rule (Eq. 1): rank
     k_i = min(k, smallest rank holding a fraction >= xi of the block's
@@ -188,15 +206,20 @@ def compress_block_xi(Ab: np.ndarray, k: int, xi: float):
     return U, s, Vt
 
 
-def compress(A: np.ndarray, b: int, k: int, incremental: bool = False, xi: float | None = None) -> Store:
+def compress(A: np.ndarray, b: int, k: int, incremental: bool = False, xi: float | None = None,
+             rowwise: bool = False) -> Store:
     """Storage phase (Algorithm 1): compress every block of A (T x n); with
-    xi, each block keeps the rank Eq. 1 gives it (at most k)."""
+    xi, each block keeps the rank Eq. 1 gives it (at most k); with rowwise,
+    every block is built row by row with truncation to rank k after each row
+    (compress_block_rowwise)."""
     A = np.asarray(A, dtype=np.float64)
     T, n = A.shape
     st = Store(b=b, n=n, k=k, T=T, U=[], s=[], Vt=[])
     if xi is not None:
         def f(Ab, kk):
             return compress_block_xi(Ab, kk, xi)
+    elif rowwise:
+        f = compress_block_rowwise
     else:
         f = compress_block_incremental if incremental else compress_block
     for lo, hi in block_bounds(T, b):

@@ -115,6 +115,70 @@ def test_algorithm1_incremental_equals_truncated_block_svd(rows, n, k):
     np.testing.assert_allclose((Ui * si) @ Vti, (Ud * sd) @ Vtd, atol=1e-10)
 
 
+# Algorithm 1 as printed: truncation to rank k after every row
+def test_rowwise_algorithm1_exact_when_block_rank_at_most_k():
+    """Data of rank <= k: no row ever loses energy, so the row-by-row result
+    is the block's exact truncated SVD (up to sign)."""
+    g = np.random.default_rng(41)
+    for rows, n, r, k in [(40, 9, 3, 3), (25, 12, 4, 6), (18, 5, 2, 4)]:
+        A = g.standard_normal((rows, r)) @ g.standard_normal((r, n))
+        dis = []
+        Uw, sw, Vtw = oracle.compress_block_rowwise(A, k, dis)
+        Ud, sd, Vtd = oracle.compress_block(A, k)
+        np.testing.assert_allclose(sw, sd, rtol=1e-11, atol=1e-12 * sd[0])
+        np.testing.assert_allclose((Uw * sw) @ Vtw, A, atol=1e-11 * np.abs(A).max())
+        np.testing.assert_allclose(Uw.T @ Uw, np.eye(Uw.shape[1]), atol=1e-12)
+        assert max(dis) <= 1e-11 * sd[0]
+
+
+def test_rowwise_algorithm1_no_truncation_when_k_covers_the_rank():
+    """k >= min(rows, n): nothing is ever discarded and the result is the
+    block's exact SVD, like Algorithm 1 without per-row truncation."""
+    g = np.random.default_rng(42)
+    A = _lowrank_noise(g, 14, 6, 3, 0.3)
+    Uw, sw, Vtw = oracle.compress_block_rowwise(A, 6)
+    _, sd, _ = np.linalg.svd(A)
+    np.testing.assert_allclose(sw, sd, rtol=1e-11)
+    np.testing.assert_allclose((Uw * sw) @ Vtw, A, atol=1e-11)
+
+
+def test_rowwise_algorithm1_energy_bookkeeping_and_bounds():
+    """Each row's truncation drops exactly one singular value of the (k+1) x n
+    stacked matrix, and blockdiag(U, 1) is orthonormal, so the energy kept
+    falls by the dropped values' squares:
+        ||A||_F^2 - ||A_hat||_F^2 = sum_t d_t^2.
+    The error is at least the Eckart-Young optimum and at most the sum of
+    the dropped values (triangle inequality over the rows)."""
+    g = np.random.default_rng(43)
+    A = _lowrank_noise(g, 60, 10, 4, 0.3)
+    dis = []
+    Uw, sw, Vtw = oracle.compress_block_rowwise(A, 4, dis)
+    Ah = (Uw * sw) @ Vtw
+    d = np.array(dis)
+    np.testing.assert_allclose(np.sum(A ** 2) - np.sum(sw ** 2), np.sum(d ** 2), rtol=1e-10)
+    err = np.linalg.norm(A - Ah)
+    _, sd, _ = np.linalg.svd(A)
+    assert err >= np.sqrt(np.sum(sd[4:] ** 2)) * (1 - 1e-12)
+    assert err <= np.sum(d) * (1 + 1e-12)
+    np.testing.assert_allclose(Uw.T @ Uw, np.eye(4), atol=1e-12)
+
+
+def test_rowwise_catches_a_planted_left_update_mistake(monkeypatch):
+    """The pins above must catch U <- [U; 0] U~ in place of blockdiag(U, 1) U~."""
+    def bad(U, s, Vt, a):
+        a = np.asarray(a, dtype=np.float64).reshape(1, -1)
+        Ut, st, Vtt = oracle.svd(np.vstack([s[:, None] * Vt, a]))
+        r, k = U.shape
+        B = np.zeros((r + 1, k + 1))
+        B[:r, :k] = U                       # the new row's "1" is missing
+        return B @ Ut, st, Vtt
+    monkeypatch.setattr(oracle.zoomsvd, "incremental_svd", bad)
+    g = np.random.default_rng(41)
+    A = g.standard_normal((40, 3)) @ g.standard_normal((3, 9))
+    Uw, sw, Vtw = oracle.compress_block_rowwise(A, 3)
+    assert not np.allclose((Uw * sw) @ Vtw, A, atol=1e-6 * np.abs(A).max())
+
+
 def test_store_lossless_reconstructs_exactly():
     g = np.random.default_rng(3)
     A = _lowrank_noise(g, 103, 8, 4)
