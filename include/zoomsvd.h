@@ -64,7 +64,18 @@ enum {
      * instead of the default for float stores with n >= 64: a bf16
      * tensor-core Gram that only locates the dominant subspace, followed by a
      * split-bf16 (~FP32) projection and Rayleigh-Ritz that sets the accuracy. */
-    ZS_FLAG_EXACT_GRAM = 2
+    ZS_FLAG_EXACT_GRAM = 2,
+    /* Algorithm 1 as printed (Section 3.2, Eq. 2-3): every appended row
+     * updates its block's rank-k SVD through the SVD of the (k+1) x n matrix
+     * [Sigma V^T; a] and U <- blockdiag(U, 1) U~, truncated back to rank k
+     * after every row - O(k^2 (rows + n)) per row (Theorem 1) instead of
+     * recompressing the open block on each append.  The stored factors are
+     * then the paper's row-by-row approximation, which equals the block's
+     * truncated SVD when the block's rank is at most k and otherwise keeps
+     * less energy (each row drops the (k+1)-th singular value of its stacked
+     * matrix).  Needs (k+1)(2n + k + 1) factor elements of shared memory
+     * (<= 227 KB); not combined with zs_store_set_xi.                     */
+    ZS_FLAG_ROW_APPEND = 4
 };
 
 typedef struct zs_store zs_store;

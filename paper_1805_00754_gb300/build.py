@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libzoomsvd.so")
 
 SOURCES = ["zs_query_f32.cu", "zs_query_f32r.cu", "zs_compress_tc.cu", "zs_compress_simt.cu", "zs_query_f64.cu",
-           "zs_launch_common.cu", "zs_api.cu", "zs_serve.cpp", "zs_noalloc.cu", "zs_similar.cu"]
+           "zs_launch_common.cu", "zs_api.cu", "zs_serve.cpp", "zs_noalloc.cu", "zs_similar.cu", "zs_rowappend.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -435,6 +435,9 @@ extern "C" zs_status zs_store_create(const zs_store_config* cfg, zs_store** out)
     const bool ref = (c.flags & ZS_FLAG_FP64_REFINE) && !fp64;
     if (!eig_plan((int)c.n, c.k, 16, fp64, ref).ok)
         return fail(ZS_EINVAL, "n=%lld with k=%d does not fit the eigen core's shared memory", (long long)c.n, c.k);
+    if ((c.flags & ZS_FLAG_ROW_APPEND) && row_append_smem_bytes((int)c.n, c.k, fp64) > 227 * 1024)
+        return fail(ZS_EINVAL, "row-by-row storage needs %zu bytes of shared memory for n=%lld, k=%d (227 KB at most)",
+                    row_append_smem_bytes((int)c.n, c.k, fp64), (long long)c.n, c.k);
     DeviceGuard g(c.device);
     zs_store* st = new zs_store();
     st->cfg = c;
@@ -492,9 +495,35 @@ extern "C" void zs_store_destroy(zs_store* st) {
 // ---------------------------------------------------------------------------
 // Storage phase.
 // ---------------------------------------------------------------------------
+// Compress blocks slot0 .. slot0 + nblk - 1 from the rows at A (row 0 of block
+// slot0 first).  The first block's rows [0, r0) were compressed before: the
+// batched path recompresses the block as it stands, the row-by-row path
+// (ZS_FLAG_ROW_APPEND) folds in only rows r0 .. onto the stored state.
 static zs_status compress_blocks(zs_store* st, const void* A, int64_t lda, int64_t rows_total, int nblk,
-                                 int64_t slot0, cudaStream_t stream, const zs_store::PipeSlot* ps = nullptr) {
+                                 int64_t slot0, cudaStream_t stream, const zs_store::PipeSlot* ps = nullptr,
+                                 int64_t r0 = 0) {
     const zs_store_config& c = st->cfg;
+    if (c.flags & ZS_FLAG_ROW_APPEND) {
+        RowAppendArgs ra;
+        memset(&ra, 0, sizeof ra);
+        ra.A = (const char*)A + (size_t)r0 * lda * st->insize;
+        ra.lda = lda;
+        ra.rows_total = rows_total - r0;
+        ra.nblk = nblk;
+        ra.slot0 = (int32_t)slot0;
+        ra.r0 = (int32_t)r0;
+        ra.in_kind = c.in_dtype;
+        ra.b = (int32_t)c.b;
+        ra.n = (int32_t)c.n;
+        ra.k = c.k;
+        ra.U = st->U;
+        ra.sig = st->sig;
+        ra.vt = st->vt;
+        ra.w = st->w;
+        cudaError_t e = launch_row_append(ra, st->fp64, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "row-by-row storage");
+        return ZS_OK;
+    }
     if (!ps && st->sub_blocks > 0 && nblk > st->sub_blocks) {
         // two-stream chunk pipeline: sub-chunk i runs on stream i % 2 with half
         // i % 2 of the scratch; both streams join back into `stream`
@@ -659,7 +688,8 @@ extern "C" zs_status zs_store_append(zs_store* st, const void* rows, int64_t nro
             return s;
         ZS_CU(cudaEventRecord(st->stage_full[0], st->copy_stream), "event");
         ZS_CU(cudaStreamWaitEvent(stream, st->stage_full[0], 0), "wait");
-        if ((s = compress_blocks(st, st->tail, c.n, tail_rows + f, 1, T / b, stream)) != ZS_OK) return s;
+        if ((s = compress_blocks(st, st->tail, c.n, tail_rows + f, 1, T / b, stream, nullptr, tail_rows)) != ZS_OK)
+            return s;
         pos = f;
         T += f;
     }
@@ -734,6 +764,8 @@ extern "C" zs_status zs_store_reset(zs_store* st) {
 extern "C" zs_status zs_store_set_xi(zs_store* st, double xi) {
     if (!st) return fail(ZS_EINVAL, "null store");
     if (!(xi >= 0.0 && xi <= 1.0)) return fail(ZS_EINVAL, "xi %g not in [0, 1]", xi);
+    if (xi > 0.0 && (st->cfg.flags & ZS_FLAG_ROW_APPEND))
+        return fail(ZS_EINVAL, "the energy rule is not combined with row-by-row storage");
     std::lock_guard<std::mutex> lk(st->mu);
     DeviceGuard g(st->cfg.device);
     if (xi > 0.0 && !st->d_energy) {

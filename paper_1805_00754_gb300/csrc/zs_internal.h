@@ -48,6 +48,27 @@ struct CompressChunk {
     int* kxi;         // xi > 0: nblk ints, each block's rank k_i as the accuracy test decided it
 };
 
+// Row-by-row storage (Algorithm 1 as printed, zs_rowappend.cu): blocks
+// slot0 .. slot0 + nblk - 1 receive the rows_total rows at A (row stride lda,
+// element type in_kind) in order; block slot0 already holds r0 rows (its
+// factors are the state), the others start empty.  nblk > 1 needs r0 == 0.
+struct RowAppendArgs {
+    const void* A;
+    int64_t lda;
+    int64_t rows_total;
+    int32_t nblk;
+    int32_t slot0;
+    int32_t r0;
+    int32_t in_kind;
+    int32_t b, n, k;
+    void* U;          // store: slot-major, b * k per slot (factor type)
+    void* sig;        // store: k per slot
+    void* vt;         // store: k * n per slot
+    void* w;          // store (tensor path, optional): Sigma V^T, k * n per slot
+};
+cudaError_t launch_row_append(const RowAppendArgs& a, bool fp64, cudaStream_t st);
+size_t row_append_smem_bytes(int n, int k, bool fp64);
+
 // Per-query plan of a batch (host-computed, then copied to the device).
 // Reading R1: rows are 0-based, ranges inclusive; S = t_s / b, E = t_e / b.
 struct QPlan {

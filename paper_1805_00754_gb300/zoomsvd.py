@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libzoomsvd.so")
 ZS_F64, ZS_F32, ZS_BF16 = 0, 1, 2
 ZS_FLAG_FP64_REFINE = 1
 ZS_FLAG_EXACT_GRAM = 2
+ZS_FLAG_ROW_APPEND = 4
 DTYPES = {"f64": ZS_F64, "f32": ZS_F32, "bf16": ZS_BF16}
 STATUS = {0: "ZS_OK", 1: "ZS_EINVAL", 2: "ZS_ERANGE", 3: "ZS_ENOMEM", 4: "ZS_EBUSY",
           5: "ZS_ETIMEDOUT", 6: "ZS_EDTYPE", 7: "ZS_ECUDA", 8: "ZS_EINTERNAL", 9: "ZS_ENOTFOUND",
@@ -150,11 +151,13 @@ class Store:
     """A compressed range-SVD store on one GPU (the sets U, S, V of Def. 2)."""
 
     def __init__(self, n: int, b: int, k: int, dtype: str = "f32", capacity_rows: int = 1 << 20,
-                 device: int = 0, fp64_refine: bool = False, exact_gram: bool = False, xi: float | None = None):
+                 device: int = 0, fp64_refine: bool = False, exact_gram: bool = False, xi: float | None = None,
+                 row_append: bool = False):
         self.n, self.b, self.k, self.dtype = n, b, k, dtype
         self.device = torch.device("cuda", device)
         self.fdtype = factor_dtype(dtype)
-        flags = (ZS_FLAG_FP64_REFINE if fp64_refine else 0) | (ZS_FLAG_EXACT_GRAM if exact_gram else 0)
+        flags = (ZS_FLAG_FP64_REFINE if fp64_refine else 0) | (ZS_FLAG_EXACT_GRAM if exact_gram else 0) | \
+            (ZS_FLAG_ROW_APPEND if row_append else 0)
         cfg = StoreConfig(n, b, k, DTYPES[dtype], capacity_rows, device, flags)
         h = C.c_void_p()
         _check(lib().zs_store_create(C.byref(cfg), C.byref(h)))

@@ -193,6 +193,18 @@ def spectrum(family: str, n: int) -> np.ndarray:
         return 0.97 ** j
     if family == "flat64":
         return np.where(j <= 64, 1.0, 0.05)
+    if family.startswith("gap"):
+        # "gapK": 1/j for the first K directions, then a floor 1e-4 j^-1/2 -
+        # a clear gap after K at every row count, so that truncating to rank
+        # K after every row (Algorithm 1 as printed) is well conditioned
+        K = int(family[3:])
+        return np.where(j <= K, 1.0 / j, 1e-4 / np.sqrt(j))
+    if family.startswith("drop"):
+        # "dropK": the same with a floor 0.1 j^-1/2 - still a gap after K,
+        # but each row's truncation drops enough energy that the row-by-row
+        # result differs visibly (~1e-5 sigma_1) from the block's truncated SVD
+        K = int(family[4:])
+        return np.where(j <= K, 1.0 / j, 0.1 / np.sqrt(j))
     raise ValueError(f"unknown spectrum family {family!r}")
 
 
