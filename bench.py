@@ -575,6 +575,9 @@ def run_gpu(args, w):
         del rows_dev
         torch.cuda.empty_cache()
         plain = plain_fp64_run(w, A, ts, te, local)
+    rowapp = None
+    if rank == 0 and not args.skip_row_append:
+        rowapp = row_append_run(w, A, local)
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = serve_run(args.serve_seconds, local, warmup=args.serve_warmup)
@@ -592,7 +595,7 @@ def run_gpu(args, w):
                 "hbm_frac_compress": compress_gbps / ws / peaks["hbm_gbs"], "space": space,
                 "accuracy_test": {"unconverged_blocks": status[0], "unconverged_queries": status[1],
                                   "refined_blocks": status[2], "refined_queries": status[3]},
-                "accuracy": acc, "serving": serving,
+                "accuracy": acc, "serving": serving, "row_append": rowapp,
                 "plain_fp32_gpu": plain32,
                 "queries_per_s_vs_plain_fp32": (qps / plain32["queries_per_s"]) if (plain32 and qps) else None,
                 "plain_fp64_gpu": plain,
@@ -863,6 +866,53 @@ def plain_fp32_run(st, ts, te, k, budget_s=2.0):
             "queries_per_s": nq / (time.perf_counter() - t0)}
 
 
+def row_append_run(w, A, local, rows_timed: int = 256, bulk_blocks: int = 304):
+    """Row-by-row storage (Algorithm 1 with truncation after every row) on the
+    workload's shape: the latency of one appended row (one call per row,
+    device rows, CUDA events on the caller's stream; the open block already
+    holds b/2 rows, so U carries b/2 .. b/2 + rows_timed rows), and the
+    throughput of folding bulk_blocks whole blocks in one call (one CTA per
+    block, rows in order within each)."""
+    import torch
+    from paper_1805_00754_gb300 import Store
+    n, b, k = w.series.n, w.b, w.k
+    itemsize = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    nb = min(bulk_blocks, A.shape[0] // b)
+    dev = torch.from_numpy(A[: nb * b]).to(f"cuda:{local}")
+    st = Store(n=n, b=b, k=k, dtype=w.dtype, capacity_rows=nb * b, device=local, row_append=True)
+    stream = torch.cuda.current_stream()
+    try:
+        half = b // 2
+        st.append(dev[:half])
+        torch.cuda.synchronize()
+        R = min(rows_timed, b - half)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(R + 1)]
+        ev[0].record(stream)
+        for r in range(R):
+            st.append(dev[half + r: half + r + 1])
+            ev[r + 1].record(stream)
+        torch.cuda.synchronize()
+        lat = np.array([ev[r].elapsed_time(ev[r + 1]) * 1e3 for r in range(R)])
+        st.reset()
+        st.append(dev[:b])                          # warm
+        torch.cuda.synchronize()
+        st.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.append(dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 1e3
+    finally:
+        st.close()
+    return {"per_row_us_mean": float(lat.mean()), "per_row_us_median": float(np.median(lat)),
+            "per_row_us_p99": float(np.percentile(lat, 99)), "rows_timed": int(R),
+            "open_block_rows_at_start": int(half),
+            "bulk_blocks": int(nb), "bulk_rows_per_s": nb * b / tb, "bulk_gbps": nb * b * n * itemsize / tb / 1e9,
+            "mode": "one zs_store_append call per row (device rows, one kernel each); bulk: one call, "
+                    "one CTA per block"}
+
+
 def serve_run(seconds: float, local: int, rate_hz: float = 20_000.0, warmup: float = 1.0):
     """Serving workload: compressed store of the serving shape, Poisson
     arrivals at rate_hz with lengths log-uniform 1e3..1e6, new blocks
@@ -962,6 +1012,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--skip-accuracy", action="store_true")
+    ap.add_argument("--skip-row-append", action="store_true", help="skip the row-by-row storage measurement")
     ap.add_argument("--skip-plain", action="store_true", help="skip the one-query-at-a-time FP64 GPU form")
     ap.add_argument("--rows", type=int, default=0, help="use the first ROWS rows (profiling small cases)")
     ap.add_argument("--sweep-b", action="store_true",

@@ -4,14 +4,22 @@
 // row).  Used for every block of a store created with ZS_FLAG_ROW_APPEND.
 //
 // One CTA per block folds the block's new rows in order.  The state of a
-// block is its stored factors: K = diag(sigma) V^T (k rows of n) and U
-// (rows x k).  For each arriving row a:
-//   1. K <- [K; a]  ((k+1) x n, the stacked matrix of Eq. 2);
-//   2. one-sided Jacobi on K's rows: rotations J make the rows orthogonal,
-//      K = J K', so that K = (J P) (P^T K') is its SVD once P sorts the rows
-//      of K' by norm (Hestenes' method on K^T);
-//   3. U <- blockdiag(U, 1) J P, keeping the first k columns (Eq. 3), and
-//      K <- the k longest rows of K' (truncation to rank k).
+// block is K = diag(sigma) V^T (k rows of n, rows orthogonal) and U (rows x k).
+// For each arriving row a:
+//   1. projection on the current right basis B = diag(1/sigma) K (the rows of
+//      V^T): p = B a, a' = a - B^T p, done twice (classical Gram-Schmidt with
+//      one reorthogonalisation), r = |a'|, q = a' / r.  Then the stacked
+//      matrix of Eq. 2 is [K; a] = M [B; q^T] with the (k+1) x (k+1) matrix
+//      M = [diag(sigma) 0; p^T r];
+//   2. one-sided Jacobi (Hestenes) on M's rows: rotations J with M = J M' and
+//      the rows of M' orthogonal; P sorts them by norm.  As [B; q^T] has
+//      orthonormal rows, [K; a] = (J P) (P^T M' [B; q^T]) is its SVD;
+//   3. truncation to rank k: K <- the k longest rows of M' [B; q^T], and
+//      U <- blockdiag(U, 1) (J P)(:, 0:k) (Eq. 3).
+// U is updated lazily: U = [U_old C; U_pend], with the k x k product C of the
+// updates since the last flush and up to kRaPend recent rows U_pend in shared
+// memory; U_old in global memory is multiplied by C once every kRaPend rows
+// and at the end of the call.
 // At the end sigma_c = |K_c|, V_c^T = K_c / sigma_c, with the sign rule R6 on
 // each pair.  Everything is in the store's factor type (FP32 or FP64).
 #include <cuda_bf16.h>
@@ -39,153 +47,386 @@ __device__ __forceinline__ T ra_eps();
 template <> __device__ __forceinline__ float ra_eps<float>() { return 1.1920929e-7f; }
 template <> __device__ __forceinline__ double ra_eps<double>() { return 2.220446049250313e-16; }
 
-// Shared memory: two K buffers ((k+1) x n each), J ((k+1) x (k+1)), the
-// pairs' rotations, norms and the sort permutation.
+constexpr int kRaPend = 64;                          // U rows kept in shared memory between flushes
+
+// Shared-memory layout (offsets in elements of the factor type; the integer
+// arrays - sort permutation and pair schedule - follow).
+struct RaLayout {
+    size_t K0, K1, arow, M, J, W, Mpp, C, C2, P, P2, sg, pv, cf, nrm, sgn, end;
+};
+__host__ __device__ __forceinline__ RaLayout ra_layout(int n, int k) {
+    const size_t m = (size_t)k + 1, kk = (size_t)k, F = kRaPend;
+    RaLayout L;
+    size_t o = 0;
+    L.K0 = o;   o += kk * n;
+    L.K1 = o;   o += kk * n;
+    L.arow = o; o += (size_t)n;
+    L.M = o;    o += m * m;
+    L.J = o;    o += m * m;
+    L.W = o;    o += m * kk;
+    L.Mpp = o;  o += kk * m;
+    L.C = o;    o += kk * kk;
+    L.C2 = o;   o += kk * kk;
+    L.P = o;    o += F * kk;
+    L.P2 = o;   o += F * kk;
+    L.sg = o;   o += 66;
+    L.pv = o;   o += 66;
+    L.cf = o;   o += 66;
+    L.nrm = o;  o += 66;
+    L.sgn = o;  o += 66;
+    L.end = o + (o & 1);
+    return L;
+}
 __host__ __device__ __forceinline__ size_t row_append_smem(int n, int k, size_t tsz) {
-    const size_t m = (size_t)k + 1;
-    return tsz * (2 * m * n + m * m + 4 * 66) + 4 * 66 + 64;
+    return tsz * ra_layout(n, k).end + 4 * 66 + 4 * 66 * 33 + 64;
+}
+
+// The Jacobi rounds give each pair of M's rows g lanes - a whole warp, or 16
+// lanes when ceil((k+1)/2) warps would pass 1024 threads (k = 63, 64): all
+// pairs of a round run at once on jt threads (whole warps).  A round is one
+// dependent chain (dot products, their reduction, the rotation, the update),
+// so fewer lanes per pair (more elements per lane) measured slower.  The
+// rest of the kernel runs on max(256, jt) threads.
+__host__ __device__ __forceinline__ int ra_group(int k) {
+    const int m = k + 1, npair = (m + (m & 1)) / 2;
+    return 32 * npair <= 1024 ? 32 : 16;
+}
+__host__ __device__ __forceinline__ int ra_jacobi_threads(int k) {
+    const int m = k + 1, npair = (m + (m & 1)) / 2;
+    return (npair * ra_group(k) + 31) / 32 * 32;
+}
+__host__ __device__ __forceinline__ int row_append_threads(int k) {
+    const int t = ra_jacobi_threads(k);
+    return t < 256 ? 256 : t;
+}
+
+// The rotation that makes rows x, y orthogonal (Hestenes): with
+// zeta = (|y|^2 - |x|^2) / (2 x.y), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1 / sqrt(1 + t^2), s = c t, tau = s / (1 + c).  In Rutishauser's form
+// the effective cosine is 1 - s tau, so an error e in c changes c^2 + s^2 by
+// O(t^2 e) only: FP32 takes the hardware reciprocal and reciprocal square
+// root here (a few ulp), FP64 the correctly rounded operations.
+__device__ __forceinline__ void rotation(float app, float aqq, float apq, float& s, float& tau) {
+    const float zeta = (aqq - app) * __frcp_rn(2.f * apq);
+    const float t = copysignf(__frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f))), zeta);
+    const float c = rsqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+    tau = s * __frcp_rn(1.f + c);
+}
+__device__ __forceinline__ void rotation(double app, double aqq, double apq, double& s, double& tau) {
+    const double zeta = (aqq - app) / (2.0 * apq);
+    const double t = copysign(1.0 / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0))), zeta);
+    const double c = 1.0 / sqrt(fma(t, t, 1.0));
+    s = c * t;
+    tau = s / (1.0 + c);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_row_append(RowAppendArgs a) {
+__device__ __forceinline__ void warp_sum2(T& a, T& b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+}
+
+// p_i = K_i . x / sigma_i and cf_i = K_i . x / sigma_i^2 for every row of K
+// (one warp per row); with norms, also sigma_i = |K_i|.
+template <typename T>
+__device__ __forceinline__ void ra_project(const T* K, const T* x, int k, int n, bool norms, T* sg, T* pv, T* cf,
+                                           int warp, int lane, int nw) {
+    for (int p = warp; p < k; p += nw) {
+        T ss = 0, pa = 0;
+        for (int l = lane; l < n; l += 32) {
+            const T v = K[(size_t)p * n + l];
+            ss += v * v;
+            pa += v * x[l];
+        }
+        warp_sum2(ss, pa);
+        if (lane == 0) {
+            if (norms) sg[p] = zsqrt(ss);
+            const T s2 = sg[p] * sg[p];
+            const bool live = sg[p] > T(0);
+            pv[p] = live ? pa / sg[p] : T(0);
+            cf[p] = live ? pa / s2 : T(0);
+        }
+    }
+}
+
+// U rows [0, r_old) <- U C diag(g) and rows [r_old, r_old + r_p) <- P diag(g)
+// (g = 1 when sg == nullptr): one warp per 4 rows, the rows' entries
+// broadcast by shuffles.
+template <typename T>
+__device__ void ra_flush(T* U, int k, int r_old, const T* C, const T* P, int r_p, const T* g, int warp, int lane,
+                         int nw, int tid, int nt) {
+    const T g0 = (g && lane < k) ? g[lane] : T(1);
+    const T g1 = (g && lane + 32 < k) ? g[lane + 32] : T(1);
+    for (int r = 4 * warp; r < r_old; r += 4 * nw) {
+        T u0[4], u1[4], o0[4], o1[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const bool in = r + h < r_old;
+            const T* ur = U + (size_t)(r + h) * k;
+            u0[h] = (in && lane < k) ? ur[lane] : T(0);
+            u1[h] = (in && lane + 32 < k) ? ur[lane + 32] : T(0);
+            o0[h] = T(0);
+            o1[h] = T(0);
+        }
+        for (int l = 0; l < k; ++l) {
+            const T c0 = lane < k ? C[(size_t)l * k + lane] : T(0);
+            const T c1 = lane + 32 < k ? C[(size_t)l * k + lane + 32] : T(0);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const T ul = __shfl_sync(0xffffffffu, l < 32 ? u0[h] : u1[h], l & 31);
+                o0[h] += ul * c0;
+                o1[h] += ul * c1;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            if (r + h >= r_old) break;
+            T* ur = U + (size_t)(r + h) * k;
+            if (lane < k) ur[lane] = o0[h] * g0;
+            if (lane + 32 < k) ur[lane + 32] = o1[h] * g1;
+        }
+    }
+    for (int e = tid; e < r_p * k; e += nt) {
+        const int c = e % k;
+        U[(size_t)r_old * k + e] = P[e] * (g ? g[c] : T(1));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_row_append(RowAppendArgs a) {
     extern __shared__ __align__(16) unsigned char ras[];
     const int j = blockIdx.x;
     if (j >= a.nblk) return;
     const int n = a.n, k = a.k, b = a.b, m = k + 1;
     const int mm = m + (m & 1), npair = mm / 2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    T* K0 = (T*)ras;
-    T* K1 = K0 + (size_t)m * n;
-    T* J = K1 + (size_t)m * n;
-    T* rot = J + (size_t)m * m;                      // c, s per pair (2 * 33)
-    T* nrm = rot + 2 * 66;                           // row norms^2 (m)
-    int* perm = (int*)(nrm + 2 * 66);
-    __shared__ int s_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x, nw = nt >> 5;
+    const RaLayout L = ra_layout(n, k);
+    T* sm = (T*)ras;
+    T* K = sm + L.K0;
+    T* Kn = sm + L.K1;
+    T* arow = sm + L.arow;
+    T* M = sm + L.M;
+    T* J = sm + L.J;
+    T* W = sm + L.W;
+    T* Mpp = sm + L.Mpp;
+    T* C = sm + L.C;
+    T* C2 = sm + L.C2;
+    T* P = sm + L.P;
+    T* P2 = sm + L.P2;
+    T* sg = sm + L.sg;
+    T* pv = sm + L.pv;
+    T* cf = sm + L.cf;
+    T* nrm = sm + L.nrm;
+    T* sgn = sm + L.sgn;
+    int* perm = (int*)(sm + L.end);
+    int* pairs = perm + 66;                          // round-robin schedule, (mm - 1) x npair
+    __shared__ T s_r;
     const int64_t slot = (int64_t)a.slot0 + j;
     T* U = (T*)a.U + slot * b * k;
     T* sig = (T*)a.sig + slot * k;
     T* Vt = (T*)a.vt + slot * k * n;
     // this block's new rows: block 0 starts at row r0 of its block
     const int r0 = j == 0 ? a.r0 : 0;
-    const T tol = T(2) * zsqrt(T(n)) * ra_eps<T>();
     const int64_t first = j == 0 ? 0 : (int64_t)b * j - a.r0;
     const int nr = (int)min((int64_t)(b - r0), a.rows_total - first);
-    T* K = K0;
-    T* Kn = K1;
-    // the state: K = diag(sigma) V^T of the rows so far (empty for a new block)
-    for (int e = tid; e < k * n; e += blockDim.x) {
-        const int c = e / n;
-        K[e] = r0 > 0 ? sig[c] * Vt[e] : T(0);
+    // a pair of M's rows counts as orthogonal once |x.y| <= 2 sqrt(k+1) eps |x||y|,
+    // the rounding level of the computed dot product itself (a smaller
+    // threshold is never met and every sweep runs)
+    const T tol = T(2) * zsqrt(T(m)) * ra_eps<T>();
+    const T tol2 = tol * tol;
+    const int g = ra_group(k), jt = ra_jacobi_threads(k);
+    for (int e = tid; e < (mm - 1) * npair; e += nt) {
+        int p, q;
+        rr_pair(mm, e / npair, e % npair, p, q);
+        pairs[e] = p | (q << 16);
     }
+    // the state: K = diag(sigma) V^T of the rows so far (empty for a new block)
+    for (int e = tid; e < k * n; e += nt) K[e] = r0 > 0 ? sig[e / n] * Vt[e] : T(0);
+    for (int e = tid; e < k * k; e += nt) C[e] = (e / k == e % k) ? T(1) : T(0);
     if (r0 == 0)
-        for (int64_t e = tid; e < (int64_t)b * k; e += blockDim.x) U[e] = T(0);
+        for (int64_t e = tid; e < (int64_t)b * k; e += nt) U[e] = T(0);
+    int r_old = r0, r_p = 0;
     __syncthreads();
     for (int i = 0; i < nr; ++i) {
-        const int rt = r0 + i;                       // the new row's index in the block
-        for (int c = tid; c < n; c += blockDim.x) K[(size_t)k * n + c] = ra_load<T>(a.A, (first + i) * a.lda + c, a.in_kind);
-        for (int e = tid; e < m * m; e += blockDim.x) J[e] = (e / m == e % m) ? T(1) : T(0);
+        for (int c = tid; c < n; c += nt) arow[c] = ra_load<T>(a.A, (first + i) * a.lda + c, a.in_kind);
         __syncthreads();
-        // ---- one-sided Jacobi on K's rows (round-robin pairs, one warp each)
-        for (int sweep = 0; sweep < 40; ++sweep) {
-            if (tid == 0) s_flag = 0;
-            __syncthreads();
-            for (int r = 0; r < mm - 1; ++r) {
-                for (int pi = warp; pi < npair; pi += nw) {
-                    int p, q;
-                    rr_pair(mm, r, pi, p, q);
-                    T s = T(0);
-                    if (q < m) {
-                        T app = 0, aqq = 0, apq = 0;
-                        for (int l = lane; l < n; l += 32) {
-                            const T x = K[(size_t)p * n + l], y = K[(size_t)q * n + l];
+        // ---- 1. p = B a, a' = a - B^T p, twice; r = |a'|, q = a' / r
+        ra_project(K, arow, k, n, true, sg, pv, cf, warp, lane, nw);
+        __syncthreads();
+        for (int l = tid; l < n; l += nt) {
+            T x = arow[l];
+            for (int c = 0; c < k; ++c) x -= cf[c] * K[(size_t)c * n + l];
+            arow[l] = x;
+        }
+        __syncthreads();
+        ra_project(K, arow, k, n, false, sg, nrm, cf, warp, lane, nw);
+        __syncthreads();
+        for (int l = tid; l < n; l += nt) {
+            T x = arow[l];
+            for (int c = 0; c < k; ++c) x -= cf[c] * K[(size_t)c * n + l];
+            arow[l] = x;
+        }
+        for (int c = tid; c < k; c += nt) pv[c] += nrm[c];
+        __syncthreads();
+        if (warp == 0) {
+            T ss = 0, dummy = 0;
+            for (int l = lane; l < n; l += 32) ss += arow[l] * arow[l];
+            warp_sum2(ss, dummy);
+            if (lane == 0) s_r = zsqrt(ss);
+        }
+        __syncthreads();
+        const T r = s_r;
+        const T rinv = r > T(0) ? T(1) / r : T(0);
+        for (int l = tid; l < n; l += nt) arow[l] *= rinv;
+        // ---- 2. M = [diag(sigma) 0; p^T r], J = I; one-sided Jacobi on M's rows
+        for (int e = tid; e < m * m; e += nt) {
+            const int row = e / m, col = e - row * m;
+            M[e] = row < k ? (row == col ? sg[row] : T(0)) : (col < k ? pv[col] : r);
+            J[e] = row == col ? T(1) : T(0);
+        }
+        __syncthreads();
+        // g lanes per pair, all pairs of a round at once; only the first jt
+        // threads (whole warps) take part and synchronise on barrier 1
+        if (tid < jt) {
+            const int pi = tid / g, sl = tid - pi * g;
+            for (int sweep = 0; sweep < 40; ++sweep) {
+                int any = 0;
+                for (int rd = 0; rd < mm - 1; ++rd) {
+                    int p = 0, q = m;
+                    if (pi < npair) {
+                        const int pq = pairs[rd * npair + pi];
+                        p = pq & 0xffff;
+                        q = pq >> 16;
+                    }
+                    const bool real = q < m;
+                    T* xp = M + (size_t)p * m;
+                    T* yq = M + (size_t)(real ? q : p) * m;
+                    T app = 0, aqq = 0, apq = 0;
+                    if (real)
+                        for (int l = sl; l < m; l += g) {
+                            const T x = xp[l], y = yq[l];
                             app += x * x;
                             aqq += y * y;
                             apq += x * y;
                         }
-                        app = warp_sum(app);
-                        aqq = warp_sum(aqq);
-                        apq = warp_sum(apq);
-                        T tau = T(0);
-                        if (apq != T(0) && zabs(apq) > tol * zsqrt(app * aqq)) {
-                            const T zeta = (aqq - app) / (T(2) * apq);
-                            const T t = (zeta >= T(0) ? T(1) : T(-1)) / (zabs(zeta) + zsqrt(T(1) + zeta * zeta));
-                            const T c = T(1) / zsqrt(T(1) + t * t);
-                            s = c * t;
-                            tau = s / (T(1) + c);
-                            if (lane == 0) s_flag = 1;
-                        }
+                    for (int o = g >> 1; o > 0; o >>= 1) {
+                        app += __shfl_xor_sync(0xffffffffu, app, o);
+                        aqq += __shfl_xor_sync(0xffffffffu, aqq, o);
+                        apq += __shfl_xor_sync(0xffffffffu, apq, o);
+                    }
+                    if (real && apq != T(0) && apq * apq > tol2 * (app * aqq)) {
+                        T s, tau;
+                        rotation(app, aqq, apq, s, tau);
+                        any = 1;
                         // Rutishauser's form of the rotation, x' = x - s (y + tau x),
-                        // y' = y + s (x - tau y), tau = s / (1 + c): c = 1 - s tau is
-                        // never rounded on its own, so small rotations do not add the
-                        // t^2 of energy per step that c rounded to 1 would
-                        if (s != T(0)) {
-                            for (int l = lane; l < n; l += 32) {
-                                const T x = K[(size_t)p * n + l], y = K[(size_t)q * n + l];
-                                K[(size_t)p * n + l] = x - s * (y + tau * x);
-                                K[(size_t)q * n + l] = y + s * (x - tau * y);
-                            }
-                            for (int l = lane; l < m; l += 32) {
-                                const T x = J[(size_t)l * m + p], y = J[(size_t)l * m + q];
-                                J[(size_t)l * m + p] = x - s * (y + tau * x);
-                                J[(size_t)l * m + q] = y + s * (x - tau * y);
-                            }
+                        // y' = y + s (x - tau y): c = 1 - s tau is never rounded on
+                        // its own, so small rotations do not add the t^2 of energy
+                        // per step that c rounded to 1 would
+                        for (int l = sl; l < m; l += g) {
+                            const T x = xp[l], y = yq[l];
+                            xp[l] = x - s * (y + tau * x);
+                            yq[l] = y + s * (x - tau * y);
+                            const T u = J[(size_t)l * m + p], v = J[(size_t)l * m + q];
+                            J[(size_t)l * m + p] = u - s * (v + tau * u);
+                            J[(size_t)l * m + q] = v + s * (u - tau * v);
                         }
                     }
+                    asm volatile("bar.sync 1, %0;" ::"r"(jt) : "memory");
                 }
-                __syncthreads();
+                int more;
+                asm volatile(
+                    "{\n\t.reg .pred pa, pr;\n\t"
+                    "setp.ne.s32 pa, %1, 0;\n\t"
+                    "bar.red.or.pred pr, 1, %2, pa;\n\t"
+                    "selp.s32 %0, 1, 0, pr;\n\t}"
+                    : "=r"(more)
+                    : "r"(any), "r"(jt)
+                    : "memory");
+                if (!more) break;
             }
-            const int f = s_flag;
-            __syncthreads();
-            if (!f) break;
-        }
-        // ---- the rows' norms and their order (descending, lower index on ties)
-        for (int p = warp; p < m; p += nw) {
-            T ss = 0;
-            for (int l = lane; l < n; l += 32) ss += K[(size_t)p * n + l] * K[(size_t)p * n + l];
-            ss = warp_sum(ss);
-            if (lane == 0) nrm[p] = ss;
         }
         __syncthreads();
-        for (int p = tid; p < m; p += blockDim.x) {
+        // ---- the rows' norms and their order (descending, lower index on ties)
+        for (int p = tid; p < m; p += nt) {
+            T ss = 0;
+            for (int l = 0; l < m; ++l) ss += M[(size_t)p * m + l] * M[(size_t)p * m + l];
+            nrm[p] = ss;
+        }
+        __syncthreads();
+        for (int p = tid; p < m; p += nt) {
             int rk = 0;
             for (int q = 0; q < m; ++q) rk += (nrm[q] > nrm[p]) || (nrm[q] == nrm[p] && q < p);
             perm[rk] = p;
         }
         __syncthreads();
-        // ---- U <- blockdiag(U, 1) J P (first k columns), one row per thread
-        for (int row = tid; row <= rt; row += blockDim.x) {
-            T out[64];
-            if (row < rt) {
-                T old[64];
-#pragma unroll 4
-                for (int c = 0; c < k; ++c) old[c] = U[(size_t)row * k + c];
-                for (int c = 0; c < k; ++c) {
-                    const int pc = perm[c];
-                    T acc = 0;
-                    for (int l = 0; l < k; ++l) acc += old[l] * J[(size_t)l * m + pc];
-                    out[c] = acc;
-                }
-            } else {
-                for (int c = 0; c < k; ++c) out[c] = J[(size_t)k * m + perm[c]];
-            }
-            for (int c = 0; c < k; ++c) U[(size_t)row * k + c] = out[c];
+        // ---- 3. W = (J P)(:, 0:k); Mpp = the kept rows of M' over [K; q] (the
+        // 1/sigma of B folded in)
+        for (int e = tid; e < m * k; e += nt) {
+            const int l = e / k, c = e - l * k;
+            W[e] = J[(size_t)l * m + perm[c]];
         }
-        // ---- K <- the k longest rows of K' (truncation to rank k)
-        for (int e = tid; e < k * n; e += blockDim.x) {
-            const int c = e / n, l = e - c * n;
-            Kn[e] = K[(size_t)perm[c] * n + l];
+        for (int e = tid; e < k * m; e += nt) {
+            const int c = e / m, l = e - c * m;
+            const T v = M[(size_t)perm[c] * m + l];
+            Mpp[e] = l == k ? v : (sg[l] > T(0) ? v / sg[l] : T(0));
+        }
+        __syncthreads();
+        // K <- Mpp [K; q^T]
+        for (int c = 0; c < k; ++c) {
+            const T* mr = Mpp + (size_t)c * m;
+            for (int l = tid; l < n; l += nt) {
+                T x = mr[k] * arow[l];
+                for (int jj = 0; jj < k; ++jj) x += mr[jj] * K[(size_t)jj * n + l];
+                Kn[(size_t)c * n + l] = x;
+            }
+        }
+        // U = [U_old C; P]: C <- C W_top, P <- [P W_top; W(k, :)]
+        for (int e = tid; e < k * k + (r_p + 1) * k; e += nt) {
+            if (e < k * k) {
+                const int row = e / k, c = e - row * k;
+                T x = 0;
+                for (int l = 0; l < k; ++l) x += C[(size_t)row * k + l] * W[(size_t)l * k + c];
+                C2[e] = x;
+            } else {
+                const int f = e - k * k, row = f / k, c = f - row * k;
+                T x = 0;
+                if (row < r_p)
+                    for (int l = 0; l < k; ++l) x += P[(size_t)row * k + l] * W[(size_t)l * k + c];
+                else
+                    x = W[(size_t)k * k + c];
+                P2[f] = x;
+            }
         }
         __syncthreads();
         T* t = K;
         K = Kn;
         Kn = t;
+        t = C;
+        C = C2;
+        C2 = t;
+        t = P;
+        P = P2;
+        P2 = t;
+        ++r_p;
+        if (r_p == kRaPend) {
+            ra_flush<T>(U, k, r_old, C, P, r_p, nullptr, warp, lane, nw, tid, nt);
+            r_old += r_p;
+            r_p = 0;
+            __syncthreads();
+            for (int e = tid; e < k * k; e += nt) C[e] = (e / k == e % k) ? T(1) : T(0);
+            __syncthreads();
+        }
     }
     // ---- outputs: sigma, V^T, Sigma V^T, with R5 (zero below the rank
     // tolerance) and R6 (largest-|.| entry of v_c positive, U flipped with it)
     for (int c = warp; c < k; c += nw) {
-        T ss = 0;
+        T ss = 0, dummy = 0;
         for (int l = lane; l < n; l += 32) ss += K[(size_t)c * n + l] * K[(size_t)c * n + l];
-        ss = warp_sum(ss);
+        warp_sum2(ss, dummy);
         if (lane == 0) nrm[c] = zsqrt(ss);
     }
     __syncthreads();
@@ -205,20 +446,19 @@ __global__ void __launch_bounds__(256) k_row_append(RowAppendArgs a) {
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        const T sg = (bi < n && K[(size_t)c * n + bi] < T(0)) ? T(-1) : T(1);
+        const T sg_ = (bi < n && K[(size_t)c * n + bi] < T(0)) ? T(-1) : T(1);
         if (lane == 0) {
             sig[c] = live ? sv : T(0);
-            rot[c] = live ? sg : T(0);               // the column's factor for U
+            sgn[c] = live ? sg_ : T(0);              // the column's factor for U
         }
         for (int l = lane; l < n; l += 32) {
-            const T v = live ? sg * K[(size_t)c * n + l] / sv : T(0);
+            const T v = live ? sg_ * K[(size_t)c * n + l] / sv : T(0);
             Vt[(size_t)c * n + l] = v;
             if (a.w) ((T*)a.w)[slot * k * n + (size_t)c * n + l] = live ? sv * v : T(0);
         }
     }
     __syncthreads();
-    const int rows = r0 + nr;
-    for (int64_t e = tid; e < (int64_t)rows * k; e += blockDim.x) U[e] *= rot[e % k];
+    ra_flush<T>(U, k, r_old, C, P, r_p, sgn, warp, lane, nw, tid, nt);
 }
 
 size_t row_append_smem_bytes(int n, int k, bool fp64) { return row_append_smem(n, k, fp64 ? 8 : 4); }
@@ -232,13 +472,13 @@ cudaError_t launch_row_append(const RowAppendArgs& a, bool fp64, cudaStream_t st
             (e = cudaFuncSetAttribute(k_row_append<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
                 cudaSuccess)
             return e;
-        k_row_append<double><<<a.nblk, 256, sm, st>>>(a);
+        k_row_append<double><<<a.nblk, row_append_threads(a.k), sm, st>>>(a);
     } else {
         if (sm > 48 * 1024 &&
             (e = cudaFuncSetAttribute(k_row_append<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
                 cudaSuccess)
             return e;
-        k_row_append<float><<<a.nblk, 256, sm, st>>>(a);
+        k_row_append<float><<<a.nblk, row_append_threads(a.k), sm, st>>>(a);
     }
     note_launches(1);
     return cudaGetLastError();
