@@ -14,9 +14,10 @@ the tolerance: the test sees the per-row truncation itself.
 The comparison is element by element with signs aligned per pair: singular
 values relative to sigma_1, V^T rows and U columns absolute, for every pair
 whose singular value is at least ``vgap`` sigma_1 from its neighbours (all
-pairs at these sizes), plus the rank-k subspace as a whole.  Append patterns: one device append of everything; host pieces of
-odd sizes (each piece continues the open block from its stored factors);
-single rows across a block boundary.  Queries over a row-by-row store are
+pairs at these sizes), plus the rank-k subspace as a whole.  Append
+patterns: one device append of everything; host pieces of odd sizes (each
+piece continues the open block from its stored factors); single rows across
+a block boundary.  Queries over a row-by-row store are
 checked against the oracle's query of its row-by-row store.
 
 Tolerances: FP64 rounding of ~b rotations per block, 2^-52 sqrt(b) |K| over
