@@ -61,10 +61,15 @@ __host__ __device__ __forceinline__ size_t ck_stage_floats(int n, int kw) {
 __host__ __device__ __forceinline__ int ck_stages(int n, int kw) {
     return 2 * ck_stage_floats(n, kw) * 4 <= 200 * 1024 ? 2 : 1;
 }
-__host__ __device__ __forceinline__ size_t ck_smem_bytes(int n, int kw) {
+// bf16 rows are copied raw (TR x round32(n) bf16) and their scale factors
+// (TR floats) per stage, then widened into the stage's fp32 tile
+__host__ __device__ __forceinline__ size_t ck_raw_floats(int n) {
+    return (size_t)ck_rows(n) * ((n + 31) / 32 * 32) / 2 + ck_rows(n);
+}
+__host__ __device__ __forceinline__ size_t ck_smem_bytes(int n, int kw, bool raw16 = false) {
     const size_t st = (size_t)ck_stages(n, kw) * ck_stage_floats(n, kw);
     const size_t rs = (size_t)(n < 512 ? (n + 15) / 16 * 16 : 512) * ((kw + 7) / 8 * 8 + 1);
-    return 4 * (st > rs ? st : rs);
+    return 4 * ((st > rs ? st : rs) + (raw16 ? (size_t)ck_stages(n, kw) * ck_raw_floats(n) : 0));
 }
 // k_refine: Q (round32(n) x ldq), then a region holding either the X and Y
 // tiles of a pass or H and Z of the Rayleigh-Ritz step
@@ -124,6 +129,48 @@ __device__ __forceinline__ void ld_xtile(const Src& src, const typename Src::Ctx
         }
         Xs[r * ldx + c] = v;
     }
+}
+
+// bf16 rows with 16-byte aligned starts (n % 8 == 0): rows [r0, r0 + nr) of
+// an item copied as they are into Rw (nr x ncp bf16) by cp.async, zero past
+// `rows` and past column n, with each row's scale factor in rs (0 for rows
+// past the item); cvt_xtile widens them into the fp32 tile once they landed.
+template <class Src>
+__device__ __forceinline__ void ld_xtile_raw16(const Src& src, const typename Src::Ctx& cx, int r0, int nr, int rows,
+                                               int n, int ncp, __nv_bfloat16* Rw, float* rs) {
+    const int q8 = ncp / 8;
+    for (int f = threadIdx.x; f < nr * q8; f += blockDim.x) {
+        const int r = f / q8, c = (f - r * q8) * 8;
+        const bool live = r0 + r < rows && c < n;
+        float sc = 0.f;
+        const __nv_bfloat16* pr = src.template row<__nv_bfloat16>(cx, min(r0 + r, rows - 1), sc);
+        cp_async16(Rw + (size_t)r * ncp + c, pr + (live ? c : 0), live ? 16 : 0);
+        if (c == 0) rs[r] = r0 + r < rows ? sc : 0.f;
+    }
+}
+__device__ __forceinline__ void cvt_xtile(const __nv_bfloat16* Rw, const float* rs, int nr, int ncp, float* Xs,
+                                          int ldx) {
+    const int q8 = ncp / 8;
+    for (int f = threadIdx.x; f < nr * q8; f += blockDim.x) {
+        const int r = f / q8, c = (f - r * q8) * 8;
+        const uint4 v = *reinterpret_cast<const uint4*>(Rw + (size_t)r * ncp + c);
+        const float sc = rs[r];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        float o[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[2 * i] = __uint_as_float(w[i] << 16) * sc;
+            o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u) * sc;
+        }
+        *reinterpret_cast<float4*>(Xs + r * ldx + c) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4*>(Xs + r * ldx + c + 4) = make_float4(o[4], o[5], o[6], o[7]);
+    }
+}
+template <class Src, typename Tin>
+__device__ __forceinline__ bool rows_raw16(const Src& src, int item, int n) {
+    if constexpr (std::is_same<Tin, __nv_bfloat16>::value)
+        return (n % 8 == 0) && (src.ld() % 8 == 0) && ((reinterpret_cast<uintptr_t>(src.X(item, 2)) & 15) == 0);
+    return false;
 }
 
 // Rows [r0, r0 + nr) of a row-major rows x w matrix B (row stride ldg) into
@@ -207,6 +254,7 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
         const float* U = src.u_out(item, kw);
         const float* vt = src.vt_out(item, kw);
         const bool vec = rows_vec16<Src, Tin>(src, item, n);
+        const bool raw = rows_raw16<Src, Tin>(src, item, n);
         if (tid < kw) {
             s_sig[tid] = src.sig_out(item, kw)[tid];
             s_rho[tid] = 0.f;
@@ -222,7 +270,13 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
                     for (int c = 0; c < 4; ++c) acc[a][b][c] = acx[a][b][c] = 0.f;
             auto issue = [&](int t) {
                 float* Xs = cks + (size_t)(t % nst) * sf;
-                ld_xtile<Src, Tin>(src, cx, t * TR, TR, rows, n, ncp, Xs, ldx, vec);
+                if (raw) {
+                    float* rw = cks + (size_t)nst * sf + (size_t)(t % nst) * ck_raw_floats(n);
+                    ld_xtile_raw16<Src>(src, cx, t * TR, TR, rows, n, ncp, reinterpret_cast<__nv_bfloat16*>(rw),
+                                        rw + (size_t)TR * ncp / 2);
+                } else {
+                    ld_xtile<Src, Tin>(src, cx, t * TR, TR, rows, n, ncp, Xs, ldx, vec);
+                }
                 ld_btile(U, kw, t * TR, TR, rows, kw, kwp, Xs + (size_t)TR * ldx, ldb);
                 cp_async_commit();
             };
@@ -237,6 +291,12 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
                     cp_async_wait<0>();
                 }
                 __syncthreads();
+                if (raw) {                                // widen the raw bf16 rows
+                    const float* rw = cks + (size_t)nst * sf + (size_t)(t % nst) * ck_raw_floats(n);
+                    cvt_xtile(reinterpret_cast<const __nv_bfloat16*>(rw), rw + (size_t)TR * ncp / 2, TR, ncp,
+                              cks + (size_t)(t % nst) * sf, ldx);
+                    __syncthreads();
+                }
                 const float* Xs = cks + (size_t)(t % nst) * sf;
                 const float* Bs = Xs + (size_t)TR * ldx;
 #pragma unroll 2

@@ -147,7 +147,7 @@ static cudaError_t certify_launch(const Src& src, const TcScratch& sc, int n, in
                                   cudaStream_t st) {
     ZS_TRY(cudaMemsetAsync(sc.list, 0, 2 * sizeof(int), st));
     {
-        const size_t sm = ck_smem_bytes(n, kw);
+        const size_t sm = ck_smem_bytes(n, kw, std::is_same<Tin, __nv_bfloat16>::value);
         int dev = 0, smem_sm = 0, resv = 0;
         ZS_TRY(cudaGetDevice(&dev));
         ZS_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
