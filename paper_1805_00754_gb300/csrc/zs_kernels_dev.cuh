@@ -624,9 +624,26 @@ __global__ void __launch_bounds__(256) k_partial(QueryArgs a) {
 #pragma unroll
             for (int s = 0; s < npair_max; ++s) {
                 if (tid + s * nt < np) {
-                    TR sacc = 0;
-                    for (int r = 0; r < nr; ++r) sacc += (TR)Us[r * ld + pa[s]] * (TR)Us[r * ld + pc[s]];
-                    acc[s] += sacc;
+                    if constexpr (REF && std::is_same<T, float>::value) {
+                        // FP64-grade sum from FP32 operations (GB300 issues FP64
+                        // at 1/64 of the FP32 rate): each product split exactly
+                        // into p + e by an FMA, the running sum kept as hi + lo
+                        // with Knuth's TwoSum, so the chunk's sum carries about
+                        // 48 significant bits before it joins acc in FP64
+                        float hi = 0.f, lo = 0.f;
+                        for (int r = 0; r < nr; ++r) {
+                            const float x = Us[r * ld + pa[s]], y = Us[r * ld + pc[s]];
+                            const float pr = x * y, pe = fmaf(x, y, -pr);
+                            const float sm = hi + pr, bb = sm - hi;
+                            lo += ((hi - (sm - bb)) + (pr - bb)) + pe;
+                            hi = sm;
+                        }
+                        acc[s] += (TR)hi + (TR)lo;
+                    } else {
+                        TR sacc = 0;
+                        for (int r = 0; r < nr; ++r) sacc += (TR)Us[r * ld + pa[s]] * (TR)Us[r * ld + pc[s]];
+                        acc[s] += sacc;
+                    }
                 }
             }
         }
