@@ -266,12 +266,13 @@ static cudaError_t tc_core(const Src& src, TcScratch sc, int n, int kw, int max_
         prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
         k_rr_core_reg<Src><<<(max_items + 3) / 4, 128, 0, st>>>(src, sc, kw);
     } else {
-        const size_t per = rr_warp_bytes<REF>(sc.m);
-        const int wpc = (int)std::min<size_t>(4, std::max<size_t>(1, (200 * 1024) / per));
-        const size_t sm = per * wpc;
+        // one item per CTA: the Jacobi rounds' rotations and the small
+        // products spread over 128 threads (one warp per item left the FP64
+        // refinement and the m > 32 sweeps latency-bound)
+        const size_t sm = rr_warp_bytes<REF>(sc.m);
         ZS_TRY(set_smem(k_rr_core<Src, REF>, sm));
         prof::Scope ps(QUERY ? "rr_core_query" : "rr_core", st);
-        k_rr_core<Src, REF><<<std::min((max_items + wpc - 1) / wpc, 65535), 32 * wpc, sm, st>>>(src, sc, kw);
+        k_rr_core<Src, REF><<<std::min(max_items, 65535), 128, sm, st>>>(src, sc, kw);
     }
     ZS_TRY(cudaGetLastError());
     {

@@ -1334,7 +1334,7 @@ __global__ void __launch_bounds__(32 * kOrthWarps) k_orth(Src src, TcScratch sc,
 }
 
 // ---------------------------------------------------------------------------
-// 4a. Rayleigh-Ritz core, one warp per item: H = sum of the tiles' Y^T Y,
+// 4a. Rayleigh-Ritz core, one CTA per item: H = sum of the tiles' Y^T Y,
 //     C = Q~^T Q~ = L L^T, H' = L^-1 H L^-T, Jacobi H' = W Theta W^T
 //     (FP32 sweeps; with REF one FP64 refinement on W^T H' W), Z = L^-T W.
 // ---------------------------------------------------------------------------
@@ -1353,8 +1353,9 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
     using TR = typename std::conditional<REF, double, float>::type;
     extern __shared__ __align__(16) char dsm[];
     const int m = sc.m, ld = m + 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-    char* base = dsm + (size_t)warp * rr_warp_bytes<REF>(m);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ JacobiScratch<float> jsf;
+    char* base = dsm;
     TR* Hs = (TR*)base;
     TR* Cs = Hs + (size_t)m * ld;
     TR* Li = Cs + (size_t)m * ld;
@@ -1364,106 +1365,103 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
     double* W = X + (REF ? (size_t)m * ld : 0);
     int* perm = (int*)(base + rr_warp_bytes<REF>(m) - 4 * 64 - 8 * 64);
     double* thd = (double*)(base + rr_warp_bytes<REF>(m) - 8 * 64);
-    char* rot = (char*)(X + (REF ? 2 * (size_t)m * ld : 0));
-    rot = (char*)(((uintptr_t)rot + 15) & ~(uintptr_t)15);
-    WarpRot<float>& wrf = *reinterpret_cast<WarpRot<float>*>(rot);
     const int count = src.count();
-    for (int item = blockIdx.x * wpc + warp; item < count; item += gridDim.x * wpc) {
+    for (int item = blockIdx.x; item < count; item += gridDim.x) {
         const int rows = src.rows(item);
         const int ntiles = (rows + 127) / 128;
         const float* Hp = sc.Hp + (size_t)src.tile0(item) * m * m;
         const float* Cq = sc.Cq + (size_t)item * m * m;
-        for (int e = lane; e < m * m; e += 32) {
+        for (int e = tid; e < m * m; e += nt) {
             TR h = 0;
             for (int t = 0; t < ntiles; ++t) h += (TR)Hp[(size_t)t * m * m + e];
             Hs[(e / m) * ld + e % m] = h;
             Cs[(e / m) * ld + e % m] = (TR)Cq[e];
         }
-        __syncwarp();
+        __syncthreads();
         // Cholesky C = L L^T (lower, in place)
         for (int j = 0; j < m; ++j) {
-            if (lane == 0) {
+            if (tid == 0) {
                 TR d = Cs[j * ld + j];
                 for (int p = 0; p < j; ++p) d -= Cs[j * ld + p] * Cs[j * ld + p];
                 Cs[j * ld + j] = d > TR(1e-12) ? (TR)sqrt((double)d) : TR(1e-6);
             }
-            __syncwarp();
-            for (int i = j + 1 + lane; i < m; i += 32) {
+            __syncthreads();
+            for (int i = j + 1 + tid; i < m; i += nt) {
                 TR d = Cs[i * ld + j];
                 for (int p = 0; p < j; ++p) d -= Cs[i * ld + p] * Cs[j * ld + p];
                 Cs[i * ld + j] = d / Cs[j * ld + j];
             }
-            __syncwarp();
+            __syncthreads();
         }
-        for (int c = lane; c < m; c += 32)
+        for (int c = tid; c < m; c += nt)
             for (int i = 0; i < m; ++i) {
                 if (i < c) { Li[i * ld + c] = 0; continue; }
                 TR d = (i == c) ? TR(1) : TR(0);
                 for (int p = c; p < i; ++p) d -= Cs[i * ld + p] * Li[p * ld + c];
                 Li[i * ld + c] = d / Cs[i * ld + i];
             }
-        __syncwarp();
+        __syncthreads();
         // H' = L^-1 H L^-T  (temp in Cs, L no longer needed)
-        for (int e = lane; e < m * m; e += 32) {
+        for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e % m;
             TR d = 0;
             for (int p = 0; p <= i; ++p) d += Li[i * ld + p] * Hs[p * ld + c];
             Cs[i * ld + c] = d;
         }
-        __syncwarp();
-        for (int e = lane; e < m * m; e += 32) {
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e % m;
             TR d = 0;
             for (int p = 0; p <= c; ++p) d += Cs[i * ld + p] * Li[c * ld + p];
             Hs[i * ld + c] = d;
         }
-        __syncwarp();
-        for (int e = lane; e < m * m; e += 32) {
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e % m;
             const TR v = (Hs[i * ld + c] + Hs[c * ld + i]) * TR(0.5);
             A_T[i * ld + c] = (float)v;
             if (REF) X[i * ld + c] = (double)v;
         }
-        __syncwarp();
-        warp_jacobi<float>(A_T, ld, Z_T, ld, m, 30, true, wrf);
+        __syncthreads();
+        jacobi_eig<float>(A_T, ld, Z_T, ld, m, jsf, 30, true);
         const double* Zsrc_d = nullptr;
         if constexpr (REF) {
             // B = Z^T H' Z in FP64 (X holds H'), then FP64 Jacobi (refinement)
             double* Hd = (double*)Hs;                    // reuse: Hs is double when REF
-            for (int e = lane; e < m * m; e += 32) {
+            for (int e = tid; e < m * m; e += nt) {
                 const int i = e / m, c = e % m;
                 double d = 0;
                 for (int l = 0; l < m; ++l) d += X[i * ld + l] * (double)Z_T[l * ld + c];
                 Hd[i * ld + c] = d;                       // H' Z
             }
-            __syncwarp();
-            for (int e = lane; e < m * m; e += 32) {
+            __syncthreads();
+            for (int e = tid; e < m * m; e += nt) {
                 const int a = e / m, c = e % m;
                 double d = 0;
                 for (int i = 0; i < m; ++i) d += (double)Z_T[i * ld + a] * Hd[i * ld + c];
                 X[a * ld + c] = d;                        // B
             }
-            __syncwarp();
+            __syncthreads();
             // one FP64 refinement sweep (closed form: B is diagonal to FP32 rounding)
-            refine_sweep<double>(X, ld, W, ld, m, lane, 32, thd, [] { __syncwarp(); });
-            for (int e = lane; e < m * m; e += 32) {
+            refine_sweep<double>(X, ld, W, ld, m, tid, nt, thd, [] { __syncthreads(); });
+            for (int e = tid; e < m * m; e += nt) {
                 const int i = e / m, c = e % m;
                 double d = 0;
                 for (int a = 0; a < m; ++a) d += (double)Z_T[i * ld + a] * W[a * ld + c];
                 Hd[i * ld + c] = d;                       // Z W
             }
-            __syncwarp();
-            warp_sort_desc<double>(X, ld, m, perm);
-            for (int c = lane; c < m; c += 32) thd[c] = X[perm[c] * ld + perm[c]];
+            __syncthreads();
+            sort_desc<double>(X, ld, m, perm);
+            for (int c = tid; c < m; c += nt) thd[c] = X[perm[c] * ld + perm[c]];
             Zsrc_d = Hd;
         } else {
-            warp_sort_desc<float>(A_T, ld, m, perm);
-            for (int c = lane; c < m; c += 32) thd[c] = (double)A_T[perm[c] * ld + perm[c]];
+            sort_desc<float>(A_T, ld, m, perm);
+            for (int c = tid; c < m; c += nt) thd[c] = (double)A_T[perm[c] * ld + perm[c]];
         }
-        __syncwarp();
+        __syncthreads();
         // Z = L^-T W(:, perm) for the kw wanted pairs
         float* Zg = sc.Zs + (size_t)item * m * kw;
-        for (int e = lane; e < m * kw; e += 32) {
+        for (int e = tid; e < m * kw; e += nt) {
             const int a = e / kw, c = e % kw;
             const int pc = perm[c];
             double d = 0;
@@ -1471,10 +1469,10 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
                 d += (double)Li[p * ld + a] * (REF ? Zsrc_d[p * ld + pc] : (double)Z_T[p * ld + pc]);
             Zg[e] = (float)d;
         }
-        for (int c = lane; c < kw; c += 32) sc.th[(size_t)item * kw + c] = (float)thd[c];
+        for (int c = tid; c < kw; c += nt) sc.th[(size_t)item * kw + c] = (float)thd[c];
         if (sc.thm)
-            for (int c = lane; c < m; c += 32) sc.thm[(size_t)item * m + c] = (float)thd[c];
-        __syncwarp();
+            for (int c = tid; c < m; c += nt) sc.thm[(size_t)item * m + c] = (float)thd[c];
+        __syncthreads();
     }
 }
 
