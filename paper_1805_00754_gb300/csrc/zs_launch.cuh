@@ -60,11 +60,14 @@ static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, 
 
 // The sketch kernel covers n <= 512 with its accumulator S (n x m) held in
 // registers: 16 NMT rows per warp, m <= MB.
-static inline bool sketch_fits(int n, int m) {
-    // n > 256 with m > 32 stays on the bf16-Gram route: its subspace (pivoted
-    // columns and a power step) is one power of X^T X ahead of the sketch's,
-    // which the precision workload's k = 32 of 40 signal directions needs
-    if (n > 512 || (n > 256 && m > 32)) return false;
+static inline bool sketch_fits(int n, int m, bool query = false) {
+    // Storage blocks with n > 256 and m > 32 stay on the bf16-Gram route:
+    // its subspace (pivoted columns and a power step) is one power of X^T X
+    // ahead of the sketch's, and on the precision workload (k = 32 of 40
+    // signal directions) the sketch left ~96% of the blocks to k_refine
+    // (measured: 20 GB/s against 61 GB/s).  Stacked query matrices pass the
+    // accuracy test from the sketch, which there beats the Gram route.
+    if (n > 512 || (!query && n > 256 && m > 32)) return false;
     return sketch_smem(n, m).total <= 227 * 1024 && (size_t)n * (m + 1) * 4 <= 227 * 1024;
 }
 
@@ -82,7 +85,8 @@ static cudaError_t sketch_dispatch(const Src& src, const TcScratch& sc, int n, i
                                     : sketch_launch<Src, Tin, 1, 64>(src, sc, n, max_items, st);
     if (n <= 256) return sc.m <= 32 ? sketch_launch<Src, Tin, 2, 32>(src, sc, n, max_items, st)
                                     : sketch_launch<Src, Tin, 2, 64>(src, sc, n, max_items, st);
-    return sketch_launch<Src, Tin, 4, 32>(src, sc, n, max_items, st);
+    return sc.m <= 32 ? sketch_launch<Src, Tin, 4, 32>(src, sc, n, max_items, st)
+                      : sketch_launch<Src, Tin, 4, 64>(src, sc, n, max_items, st);
 }
 
 template <class Src, int RPL, int CPW>
@@ -209,7 +213,7 @@ static cudaError_t tc_core(const Src& src, TcScratch sc, int n, int kw, int max_
     const int npairs = ntile * (ntile + 1) / 2;
     const int gi = std::min(max_items, 65535);
     const int proj_per_sm = tu.project_ctas_per_sm;
-    if (tu.fused_sketch && sketch_fits(n, sc.m)) {
+    if (tu.fused_sketch && sketch_fits(n, sc.m, QUERY)) {
         {
             prof::Scope ps(QUERY ? "sketch_query" : "sketch", st);
             ZS_TRY((sketch_dispatch<Src, Tin>(src, sc, n, max_items, st)));
