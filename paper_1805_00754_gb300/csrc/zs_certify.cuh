@@ -222,9 +222,67 @@ __device__ __forceinline__ bool cert_pass(const float* sig, const float* rho, in
 }
 
 // ---------------------------------------------------------------------------
+// Work units of k_check on stacked query matrices, whose rows differ by 30x
+// within a batch: a matrix of more than kCheckPartRows rows is cut into up to
+// n / kwp parts of whole 32-row tiles, so that the largest query no longer
+// runs alone on one SM.  Each part's partial X^T U (n x kwp) goes to the
+// item's n x n scratch G (free once the basis is formed; the refinement that
+// reuses it runs after the test), and the CTA that finishes an item's last
+// part sums the parts in part order and applies the test.  cplan: the
+// exclusive prefix of the items' part counts (count + 1 entries), then one
+// arrival counter per item, zeroed here.
+// ---------------------------------------------------------------------------
+constexpr int kCheckPartRows = 512;
+template <class Src>
+__global__ void __launch_bounds__(1024) k_check_plan(Src src, TcScratch sc, int n, int kw) {
+    __shared__ int s_carry, s_warp[32];
+    const int count = src.count();
+    const int kwp = (kw + 7) / 8 * 8, pmax = max(1, n / kwp);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int* pre = sc.cplan;
+    int* arrive = sc.cplan + count + 1;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < count; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int v = 0;
+        if (i < count) {
+            const int rows = src.rows(i);
+            v = rows > kCheckPartRows ? min(pmax, (rows + kCheckPartRows - 1) / kCheckPartRows) : 1;
+            arrive[i] = 0;
+        }
+        int x = v;                                    // inclusive scan: warp, then across warps
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nwarp ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (i < count) pre[i] = s_carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pre[count] = s_carry;
+}
+
+// ---------------------------------------------------------------------------
 // k_check: R = X^T U by column blocks of X of up to 512 (NTW <= 4 16-row tiles
 // of R per warp, KT <= 8 column tiles of 8: kw <= 8 KT), each block one sweep
-// over the item's rows; rho_j^2 accumulates over the blocks.
+// over the unit's rows; rho_j^2 accumulates over the blocks.  A unit is an
+// item, or (stacked query matrices, sc.cplan set) a part of one.
 // ---------------------------------------------------------------------------
 template <class Src, typename Tin, int NTW, int KT>
 __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 2 : 1))
@@ -240,15 +298,33 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
     const int nst = ck_stages(n, kw);
     const size_t sf = ck_stage_floats(n, kw);
     const int m = sc.m;
-    __shared__ int s_item;
+    __shared__ int s_item, s_last;
+    const bool split = std::is_same<Src, SrcQuery>::value && sc.cplan != nullptr;
     for (;;) {
-        // items are handed out one at a time (their sizes differ by 30x in a query batch)
-        __syncthreads();                                  // the previous item's shared data are consumed
+        // units are handed out one at a time (item sizes differ by 30x in a query batch)
+        __syncthreads();                                  // the previous unit's shared data are consumed
         if (tid == 0) s_item = atomicAdd(sc.list + 1, 1);
         __syncthreads();
-        const int item = s_item;
-        if (item >= src.count()) break;
-        const int rows = src.rows(item);
+        int item = s_item, part = 0, nparts = 1;
+        if (split) {
+            const int u = s_item, count = src.count();
+            if (u >= sc.cplan[count]) break;
+            int lo = 0, hi = count - 1;                   // the last item whose first unit is <= u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sc.cplan[mid] <= u) lo = mid; else hi = mid - 1;
+            }
+            item = lo;
+            part = u - sc.cplan[item];
+            nparts = sc.cplan[item + 1] - sc.cplan[item];
+        } else if (item >= src.count()) {
+            break;
+        }
+        const int rows_all = src.rows(item);
+        // this unit's rows [r_lo, rows): whole TR-row tiles per part
+        const int prr = nparts > 1 ? ((rows_all + nparts - 1) / nparts + TR - 1) / TR * TR : rows_all;
+        const int r_lo = min(rows_all, part * prr);
+        const int rows = min(rows_all, r_lo + prr);
         const int kc = src.kcap(item, kw);
         const auto cx = src.ctx(item, sizeof(Tin));
         const float* U = src.u_out(item, kw);
@@ -259,7 +335,23 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
             s_sig[tid] = src.sig_out(item, kw)[tid];
             s_rho[tid] = 0.f;
         }
-        const int ntl = (rows + TR - 1) / TR;
+        const int ntl = (rows - r_lo + TR - 1) / TR;
+        float* Rpart = split ? sc.G + (size_t)item * n * n + (size_t)part * n * kwp : nullptr;
+        // this block of R rows through shared memory, then its share of rho_j^2
+        auto rho_block = [&](int i0, int i1) {
+            const float* Rs = cks;
+            const int ldr = kwp + 1;
+            for (int j = warp; j < kw; j += 8) {
+                const float sj = s_sig[j];
+                float ss = 0.f;
+                for (int l = i0 + lane; l < i1; l += 32) {
+                    const float d = Rs[(l - i0) * ldr + j] - sj * vt[(size_t)j * n + l];
+                    ss = fmaf(d, d, ss);
+                }
+                ss = warp_sum(ss);
+                if (lane == 0) s_rho[j] += ss;
+            }
+        };
         for (int mt0 = 0; mt0 < nmt; mt0 += 8 * NTW) {
             float acc[NTW][KT][4], acx[NTW][KT][4];
 #pragma unroll
@@ -272,12 +364,12 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
                 float* Xs = cks + (size_t)(t % nst) * sf;
                 if (raw) {
                     float* rw = cks + (size_t)nst * sf + (size_t)(t % nst) * ck_raw_floats(n);
-                    ld_xtile_raw16<Src>(src, cx, t * TR, TR, rows, n, ncp, reinterpret_cast<__nv_bfloat16*>(rw),
-                                        rw + (size_t)TR * ncp / 2);
+                    ld_xtile_raw16<Src>(src, cx, r_lo + t * TR, TR, rows, n, ncp,
+                                        reinterpret_cast<__nv_bfloat16*>(rw), rw + (size_t)TR * ncp / 2);
                 } else {
-                    ld_xtile<Src, Tin>(src, cx, t * TR, TR, rows, n, ncp, Xs, ldx, vec);
+                    ld_xtile<Src, Tin>(src, cx, r_lo + t * TR, TR, rows, n, ncp, Xs, ldx, vec);
                 }
-                ld_btile(U, kw, t * TR, TR, rows, kw, kwp, Xs + (size_t)TR * ldx, ldb);
+                ld_btile(U, kw, r_lo + t * TR, TR, rows, kw, kwp, Xs + (size_t)TR * ldx, ldb);
                 cp_async_commit();
             };
             __syncthreads();                              // the residual step below has read the stages
@@ -334,7 +426,6 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
             }
             cp_async_wait<0>();
             __syncthreads();
-            // this block of R rows through shared memory, then its share of rho_j^2
             float* Rs = cks;
             const int ldr = kwp + 1;
             const int i0 = mt0 * 16, i1 = min(n, (mt0 + 8 * NTW) * 16);
@@ -348,20 +439,38 @@ __global__ void __launch_bounds__(256, (NTW * KT <= 4) ? 3 : ((NTW * KT <= 8) ? 
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int i = mt * 16 + g + ((e >> 1) ? 8 : 0), j = nt * 8 + 2 * t4 + (e & 1);
-                        if (i < n) Rs[(i - i0) * ldr + j] = acc[mi][nt][e] + acx[mi][nt][e];
+                        if (i >= n) continue;
+                        if (nparts > 1) Rpart[(size_t)i * kwp + j] = acc[mi][nt][e] + acx[mi][nt][e];
+                        else Rs[(i - i0) * ldr + j] = acc[mi][nt][e] + acx[mi][nt][e];
                     }
                 }
             }
             __syncthreads();
-            for (int j = warp; j < kw; j += 8) {
-                const float sj = s_sig[j];
-                float ss = 0.f;
-                for (int l = i0 + lane; l < i1; l += 32) {
-                    const float d = Rs[(l - i0) * ldr + j] - sj * vt[(size_t)j * n + l];
-                    ss = fmaf(d, d, ss);
+            if (nparts == 1) rho_block(i0, i1);
+        }
+        if (nparts > 1) {
+            // publish this part; the CTA that brings the item's last part sums
+            // all parts in part order and applies the test
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(sc.cplan + src.count() + 1 + item, 1) == nparts - 1;
+            __syncthreads();
+            if (!s_last) continue;
+            __threadfence();
+            const float* Ritem = sc.G + (size_t)item * n * n;
+            for (int mt0 = 0; mt0 < nmt; mt0 += 8 * NTW) {
+                const int i0 = mt0 * 16, i1 = min(n, (mt0 + 8 * NTW) * 16);
+                float* Rs = cks;
+                const int ldr = kwp + 1;
+                __syncthreads();
+                for (int e = tid; e < (i1 - i0) * kwp; e += blockDim.x) {
+                    const int i = i0 + e / kwp, j = e - (e / kwp) * kwp;
+                    float r = 0.f;
+                    for (int q = 0; q < nparts; ++q) r += __ldcg(Ritem + (size_t)q * n * kwp + (size_t)i * kwp + j);
+                    Rs[(i - i0) * ldr + j] = r;
                 }
-                ss = warp_sum(ss);
-                if (lane == 0) s_rho[j] += ss;
+                __syncthreads();
+                rho_block(i0, i1);
             }
         }
         __syncthreads();

@@ -56,6 +56,8 @@ static inline void tc_aux_carve(void* aux, int64_t items, int64_t tiles, int m, 
     sc.thm = (float*)p;
     p += r(4 * (size_t)items * m);
     sc.list = (int*)p;
+    p += r(4 * (size_t)(items + 2));
+    sc.cplan = (int*)p;
 }
 
 // The sketch kernel covers n <= 512 with its accumulator S (n x m) held in
@@ -150,6 +152,8 @@ template <class Src, typename Tin>
 static cudaError_t certify_launch(const Src& src, const TcScratch& sc, int n, int kw, int max_items, int num_sms,
                                   cudaStream_t st) {
     ZS_TRY(cudaMemsetAsync(sc.list, 0, 2 * sizeof(int), st));
+    TcScratch scc = sc;
+    scc.cplan = nullptr;
     {
         const size_t sm = ck_smem_bytes(n, kw, std::is_same<Tin, __nv_bfloat16>::value);
         int dev = 0, smem_sm = 0, resv = 0;
@@ -157,11 +161,23 @@ static cudaError_t certify_launch(const Src& src, const TcScratch& sc, int n, in
         ZS_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
         ZS_TRY(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
         const int per_sm = std::max(1, std::min(4, smem_sm / (int)(sm + 1024 + resv)));
-        const int grid = std::max(1, std::min(max_items, num_sms * per_sm));
+        if constexpr (std::is_same<Src, SrcQuery>::value) {
+            // stacked matrices cut into parts where a batch has too few queries
+            // to balance the SMs by itself (measured: 0.76 -> 0.65 ms at 1,024
+            // queries; at 4,096 and 20,000 queries the parts only cost); the
+            // items' n x n scratch must hold n / kwp partial results
+            if (max_items < 4 * num_sms * per_sm && n >= 2 * ((kw + 7) / 8 * 8)) {
+                scc.cplan = sc.cplan;
+                k_check_plan<Src><<<1, 1024, 0, st>>>(src, sc, n, kw);
+                ZS_TRY(cudaGetLastError());
+            }
+        }
+        // parts of stacked query matrices outnumber the items: a full persistent grid there
+        const int grid = std::max(1, scc.cplan ? num_sms * per_sm : std::min(max_items, num_sms * per_sm));
         prof::Scope ps(std::is_same<Src, SrcQuery>::value ? "check_query" : "check", st);
         auto go = [&](auto kern) -> cudaError_t {
             ZS_TRY(set_smem(kern, sm));
-            kern<<<grid, 256, sm, st>>>(src, sc, n, kw);
+            kern<<<grid, 256, sm, st>>>(src, scc, n, kw);
             return cudaGetLastError();
         };
         // 16-row tiles of R per warp: 1 (n <= 128), 2 (n <= 256), 4 (blocks of 512 columns)

@@ -143,7 +143,8 @@ size_t eig_ws_bytes(int n, bool fp64, int ctas) {
 size_t tc_aux_bytes(int64_t items, int64_t tiles, int m, int kw) {
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     return r(4 * (size_t)tiles * m * m) + r(4 * (size_t)items * m * m) + r(4 * (size_t)items * m * kw) +
-           r(4 * (size_t)items * kw) + r(4 * (size_t)items * m) + r(4 * (size_t)(items + 2));
+           r(4 * (size_t)items * kw) + r(4 * (size_t)items * m) + r(4 * (size_t)(items + 2)) +
+           r(4 * (size_t)(2 * items + 1));
 }
 
 cudaError_t launch_compress_simt(const CompressChunk& c, bool fp64, int flags, const Tuning& tu, int num_sms,

@@ -152,6 +152,7 @@ struct TcScratch {
     float* th;              // items x kw: Ritz values (sigma^2)
     float* thm;             // items x m: all m Ritz values, descending (accuracy test)
     int* list;              // 2 + items ints: count, work counter, then the items that failed the accuracy test
+    int* cplan;             // 2 items + 1 ints: k_check's part plan for stacked query matrices (or null)
     int* noconv;            // incremented per item whose refinement stopped at its pass cap (or null)
     int* refined;           // incremented per item refined (or null)
     double xi;              // storage phase, xi > 0: energy rule (Eq. 1); only ranks < k_i are tested
