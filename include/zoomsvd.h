@@ -147,10 +147,12 @@ zs_status zs_store_info(const zs_store* st, int64_t* rows, int64_t* nblocks,
  * gives block i the rank k_i = the smallest rank whose leading singular
  * values hold a fraction >= xi of ||X_i||_F^2 (the sum of all the block's
  * sigma_j^2), capped at the store's k; columns k_i.. of its U, sigma and V
- * are stored as zeros (the arrays keep width k), which queries treat as rank
+ * are stored as zeros (the arrays keep width k).  While xi > 0, queries on
+ * float stores with n >= 64 stack only the live rows (nonzero sigma) of each
+ * interior block (ragged stacks); other stores treat the zero rows as rank
  * deficiency.  xi = 0 restores the fixed rank k.  Costs one more read of each
  * block's rows per append.  ZS_EINVAL for xi outside [0, 1], ZS_ENOMEM if the
- * per-block scratch (8 bytes per block of capacity) cannot be allocated.    */
+ * per-block scratch (12 bytes per block of capacity) cannot be allocated.   */
 zs_status zs_store_set_xi(zs_store* st, double xi);
 
 /* Per-block ranks and energies (Eq. 1; Theorem 3; the reconstruction error

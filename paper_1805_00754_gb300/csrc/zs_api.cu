@@ -73,8 +73,9 @@ void QueryExec::release() {
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
     if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
     g_kq = g_kout = -1;
+    g_ragged = -1;
     w_kq = w_kout = -1;
-    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C); f(ews); f(qb); f(ys); f(aux);
+    f(d_blob); f(M); f(G); f(sr); f(vr); f(tco); f(C); f(ews); f(qb); f(ys); f(aux); f(rowmap); f(Cc); f(kpre);
     fh(h_blob);
     cap_nq = 0;
     cap_slabs = 0;
@@ -253,15 +254,38 @@ zs_status run_batch(zs_store& st, QueryExec& x, int64_t Trows, std::vector<QPlan
     a.ys = x.ys;
     a.aux = x.aux;
     a.aux_tiles = x.aux_tiles;
+    // ragged stacks on energy-rule stores of the tensor path (interior slabs
+    // contribute their live rows only)
+    const int ragged = (st.xi > 0.0 && st.w && use_tc_path(st.fp64, (int)st.cfg.n, st.cfg.flags)) ? 1 : 0;
+    if (ragged && !x.rowmap) {
+        const size_t rows = (size_t)x.cap_slabs * st.cfg.k;
+        cudaError_t e = cudaMalloc(&x.rowmap, std::max<size_t>(4 * rows, 256));
+        if (e == cudaSuccess) e = cudaMalloc(&x.Cc, std::max<size_t>(st.tsize * rows * x.cap_kq, 256));
+        if (e == cudaSuccess) e = cudaMalloc(&x.kpre, sizeof(int64_t) * (size_t)(st.cap_blocks + 1));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (x.rowmap) cudaFree(x.rowmap);
+            if (x.Cc) cudaFree(x.Cc);
+            x.rowmap = x.Cc = nullptr;
+            return fail(ZS_ENOMEM, "query scratch (ragged stack row map)");
+        }
+    }
+    if (ragged) {
+        a.kpre = (int64_t*)x.kpre;
+        a.rowmap = (int*)x.rowmap;
+        a.Cc = x.Cc;
+    }
     int max_rows = 0;
     for (const QPlan& P : plans) max_rows = std::max(max_rows, P.nslab * (int)st.cfg.k);
     // the first batch of a (k_q, k_out) shape runs eagerly (it also sets the
     // kernels' attributes); later ones replay a captured graph
-    const bool warm = (x.w_kq == kq && x.w_kout == kout && x.w_lift == lift);
+    const bool warm = (x.w_kq == kq && x.w_kout == kout && x.w_lift == lift && x.g_ragged == ragged);
     if (profiling_on() || !st.use_graphs || !warm) {
         x.w_kq = kq;
         x.w_kout = kout;
         x.w_lift = lift;
+        if (x.g_ragged != ragged && x.gexec) { cudaGraphExecDestroy(x.gexec); x.gexec = nullptr; }
+        x.g_ragged = ragged;
         // eager: grids sized to this batch (the profiler brackets each launch)
         ZS_CU(cudaMemcpyAsync(x.d_blob, x.h_blob, bytes, cudaMemcpyHostToDevice, stream), "plan upload");
         QueryGrid g{nq, nslab, ntiles, max_rows};

@@ -27,12 +27,15 @@ struct QueryExec {
     void* ys = nullptr;
     void* aux = nullptr;
     int64_t aux_tiles = 0;
+    void* rowmap = nullptr;       // ragged stacks (energy-rule stores): cap_slabs x k ints
+    void* Cc = nullptr;           // ragged stacks: compact U_r, cap_slabs x k x cap_kq
+    void* kpre = nullptr;         // ragged stacks: prefix of the blocks' live ranks (store capacity + 1)
     cudaEvent_t done = nullptr;   // last batch that used this scratch
     // one captured launch set (plan upload + all query kernels) for this
     // executor's capacity, replayed for every batch that fits it
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    int g_kq = -1, g_kout = -1, g_lift = -1;
+    int g_kq = -1, g_kout = -1, g_lift = -1, g_ragged = -1;
     int w_kq = -1, w_kout = -1, w_lift = -1;   // shape of the last eager batch
     int64_t g_launches = 0;
     ~QueryExec();

@@ -140,6 +140,15 @@ struct QueryArgs {
     int* fault;       // device word set to 1 when a bounded wait gives up (or null)
     int* noconv;      // device count of queries whose refinement stopped at its pass cap (or null)
     int* refined;     // device count of queries that needed refinement (or null)
+    // ragged stacks (energy-rule stores on the tensor path; else null): interior
+    // slabs contribute only their live rows; kpre (blocks + 1) is the prefix of
+    // the stored blocks' live ranks, formed at the start of each batch; rowmap
+    // maps each stacked row to its source (>= 0: row of the store's Sigma V^T,
+    // < 0: -1 - row of M), and the stitched U_r lands compact in Cc before it
+    // is spread to C
+    int64_t* kpre;
+    int* rowmap;      // slab capacity x k ints, at slab0 * k per query
+    void* Cc;         // slab capacity x k x kq
 };
 
 // Launch configuration chosen by the autotuner (or defaults).

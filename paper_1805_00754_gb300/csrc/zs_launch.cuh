@@ -140,7 +140,8 @@ static bool t5_maps(const SrcCompress& s, int n, T5Maps& mp) {
 }
 // 8-row boxes stay inside one slab when k % 8 == 0
 static bool t5_maps(const SrcQuery& s, int n, T5Maps& mp) {
-    if (s.a.k % 8 != 0) return false;
+    // ragged stacks: rows come through the row map, not in 8-row slab boxes
+    if (s.a.k % 8 != 0 || s.a.rowmap) return false;
     if (!t5_map(&mp.x0, s.a.M, s.a.m_rows, n, n, 8)) return false;
     return s.a.wst ? t5_map(&mp.x1, s.a.wst, s.a.w_rows, n, n, 8) : t5_map(&mp.x1, s.a.M, s.a.m_rows, n, n, 8);
 }
@@ -402,9 +403,22 @@ static cudaError_t query_impl(const QueryArgs& a, const QueryGrid& g, int flags,
             sc.energy = nullptr;
             sc.kxi = nullptr;
             SrcQuery src{a};
+            if (a.rowmap) {
+                prof::Scope ps("ragged_map", st);
+                k_ragged_prefix<<<1, 1024, 0, st>>>(a);
+                k_ragged_map<<<std::min(max_nq, pers), 256, 0, st>>>(a);
+                ZS_TRY(cudaGetLastError());
+                note_launches(2);
+            }
             // stacked rows (M and the store's Sigma V^T) are 16-byte aligned when n % 4 == 0
             ZS_TRY((tc_core<SrcQuery, float, REF, true>(src, sc, n, kq, max_nq, g.tiles, sc.ews_ctas, num_sms,
                                                         tu, st, n % 4 == 0)));
+            if (a.rowmap) {
+                prof::Scope ps("ragged_expand", st);
+                k_ragged_expand<<<std::min(max_nq, pers), 256, 0, st>>>(a);
+                ZS_TRY(cudaGetLastError());
+                note_launches(1);
+            }
             {
                 const size_t sm = sizeof(float) * ((size_t)k * k + (size_t)k * kq);
                 ZS_TRY(set_smem(k_bfix, sm));

@@ -86,7 +86,11 @@ struct SrcCompress {
 struct SrcQuery {
     QueryArgs a;
     __device__ __forceinline__ int count() const { return a.hdr->nq; }
-    __device__ __forceinline__ int rows(int q) const { return a.plans[q].nslab * a.k; }
+    // ragged stacks (a.rowmap): the stacked row count that k_ragged_map
+    // recorded in the plan; otherwise k rows per slab
+    __device__ __forceinline__ int rows(int q) const {
+        return a.rowmap ? a.plans[q].pad1 : a.plans[q].nslab * a.k;
+    }
     __device__ __forceinline__ int64_t ld() const { return a.n; }
     __device__ __forceinline__ const void* X(int q, int elem) const {
         return (const char*)a.M + (size_t)a.plans[q].slab0 * a.k * a.n * elem;
@@ -98,16 +102,21 @@ struct SrcQuery {
     // them (wst) and otherwise copied into M by the stack kernel.
     // kmagic = ceil(2^32 / k): the slab of row r is umulhi(r, kmagic), exact
     // for r < 2^32 / k (no integer division per row)
-    struct Ctx { const char* base; const char* wbase; int nslab; uint32_t kmagic; };
+    struct Ctx { const char* base; const char* wbase; int nslab; uint32_t kmagic; const int* map; };
     __device__ __forceinline__ Ctx ctx(int q, int elem) const {
         const QPlan& P = a.plans[q];
         return Ctx{(const char*)a.M + (size_t)P.slab0 * a.k * a.n * elem,
                    a.wst ? (const char*)a.wst + (size_t)P.S * a.k * a.n * elem : nullptr, P.nslab,
-                   (uint32_t)((0x100000000ull + (uint64_t)a.k - 1) / (uint64_t)a.k)};
+                   (uint32_t)((0x100000000ull + (uint64_t)a.k - 1) / (uint64_t)a.k),
+                   a.rowmap ? a.rowmap + P.slab0 * a.k : nullptr};
     }
     template <typename Tin>
     __device__ __forceinline__ const Tin* row(const Ctx& x, int r, float& scale) const {
         scale = 1.f;
+        if (x.map) {              // ragged: the row map names the source row
+            const int v = x.map[r];
+            return v >= 0 ? (const Tin*)a.wst + (size_t)v * a.n : (const Tin*)a.M + (size_t)(-1 - v) * a.n;
+        }
         if (x.wbase) {
             const int t = (int)__umulhi((uint32_t)r, x.kmagic);
             if (t > 0 && t < x.nslab - 1) return (const Tin*)x.wbase + (size_t)r * a.n;
@@ -117,7 +126,7 @@ struct SrcQuery {
     // the stitched factors of query q: U_r rows = the lift coefficients C
     // (row stride kq), sigma (kq), V_r^T (kq x n); kcap from the plan
     __device__ __forceinline__ float* u_out(int q, int kw) const {
-        return (float*)a.C + (size_t)a.plans[q].slab0 * a.k * kw;
+        return (float*)(a.rowmap ? a.Cc : a.C) + (size_t)a.plans[q].slab0 * a.k * kw;
     }
     __device__ __forceinline__ float* sig_out(int q, int kw) const { return (float*)a.sr + (size_t)q * kw; }
     __device__ __forceinline__ float* vt_out(int q, int kw) const { return (float*)a.vr + (size_t)q * kw * a.n; }
@@ -1675,7 +1684,7 @@ __global__ void __launch_bounds__(256) k_rr_out(Src src, TcScratch sc, int n, in
         if constexpr (QUERY) {
             const QPlan& P = src.a.plans[item];
             vt_out = (float*)src.a.vr + (size_t)item * src.a.kq * n;
-            u_out = (float*)src.a.C + (size_t)P.slab0 * src.a.k * src.a.kq;
+            u_out = src.u_out(item, src.a.kq);        // C, or the compact Cc of a ragged stack
             urows = rows;
             float* sr = (float*)src.a.sr + (size_t)item * src.a.kq;
             for (int c = tid; c < src.a.kout; c += nt) {
@@ -2214,6 +2223,114 @@ __global__ void __launch_bounds__(128) k_partial_warp(QueryArgs a) {
                     Ms[(int64_t)j * n + ll] = sj > 0.f ? sj * c[mt][e] : 0.f;
                 }
             }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ragged stacks (energy rule, Eq. 1): the stacked matrix of a query takes the
+// two boundary slabs' k rows (Partial-SVD output in M) and only the live rows
+// of the interior slabs - block s contributes kpre[s + 1] - kpre[s] rows of
+// its stored Sigma_s V_s^T, the rest being zero rows that change no result.
+// k_ragged_map writes each query's row map (>= 0: row of the store's
+// Sigma V^T, < 0: -1 - row of M) and its row count (plan.pad1); after the
+// stitched SVD, k_ragged_expand spreads the compact U_r rows back to k rows
+// per slab (zero for the dropped rows) for the boundary fix and the lift.
+// One CTA per query.
+// ---------------------------------------------------------------------------
+// kpre[i] = live ranks (nonzero sigma: the energy rule and R5 zero the rest)
+// of blocks 0 .. i-1 of the store's T rows; one CTA, a block-wide scan per
+// 1,024 blocks.
+static __global__ void __launch_bounds__(1024) k_ragged_prefix(QueryArgs a) {
+    __shared__ int64_t s_carry;
+    __shared__ int s_warp[32];
+    const int k = a.k;
+    const int64_t nblk = (a.hdr->T + a.b - 1) / a.b;
+    const float* sig = (const float*)a.sig;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        a.kpre[0] = 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < nblk; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int v = 0;
+        if (i < nblk)
+            for (int j = 0; j < k; ++j) v += sig[i * k + j] > 0.f;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nwarp ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (warp > 0 ? s_warp[warp - 1] : 0);
+        if (i < nblk) a.kpre[i + 1] = s_carry + incl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry += incl;
+        __syncthreads();
+    }
+}
+
+static __global__ void __launch_bounds__(256) k_ragged_map(QueryArgs a) {
+    const int k = a.k, nq = a.hdr->nq;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        QPlan& P = const_cast<QPlan&>(a.plans[q]);
+        const int64_t base = P.slab0 * k;
+        int* map = a.rowmap + base;
+        const int ns = P.nslab;
+        int R = k;
+        if (ns == 1) {
+            for (int r = threadIdx.x; r < k; r += blockDim.x) map[r] = (int)(-1 - (base + r));
+        } else {
+            const int64_t K0 = a.kpre[P.S + 1];
+            R = 2 * k + (int)(a.kpre[P.S + ns - 1] - K0);
+            for (int r = threadIdx.x; r < k; r += blockDim.x) {
+                map[r] = (int)(-1 - (base + r));
+                map[R - k + r] = (int)(-1 - (base + (int64_t)(ns - 1) * k + r));
+            }
+            for (int e = threadIdx.x; e < (ns - 2) * k; e += blockDim.x) {
+                const int t = 1 + e / k, j = e - (e / k) * k;
+                const int64_t s = P.S + t;
+                const int64_t lo = a.kpre[s];
+                if (j < (int)(a.kpre[s + 1] - lo)) map[k + (lo - K0) + j] = (int)(s * k + j);
+            }
+        }
+        if (threadIdx.x == 0) P.pad1 = R;
+    }
+}
+
+static __global__ void __launch_bounds__(256) k_ragged_expand(QueryArgs a) {
+    const int k = a.k, kq = a.kq, nq = a.hdr->nq;
+    for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+        const QPlan& P = a.plans[q];
+        const int64_t base = P.slab0 * k;
+        float* C = (float*)a.C + base * kq;
+        const float* Cc = (const float*)a.Cc + base * kq;
+        const int* map = a.rowmap + base;
+        const int R = P.pad1;
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < (int64_t)P.nslab * k * kq; e += blockDim.x) C[e] = 0.f;
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * kq; e += blockDim.x) {
+            const int r = e / kq, c = e - (e / kq) * kq;
+            const int v = map[r];
+            int64_t dst;                                 // the row's place in the slab layout
+            if (v >= 0) dst = (int64_t)(v / k - P.S) * k + v % k;
+            else dst = (int64_t)(-1 - v) - base;
+            C[dst * kq + c] = Cc[(int64_t)r * kq + c];
+        }
     }
 }
 

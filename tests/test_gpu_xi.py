@@ -134,3 +134,75 @@ def test_xi_errors_and_reset_to_fixed():
         st.set_xi(1.5)
     assert e.value.status == 1
     st.set_xi(0.0)                       # fixed rank again
+
+
+def test_ragged_stack_full_ranks_reproduce_the_plain_stack():
+    """With xi = 1 every block keeps k_i = k, so the ragged stack (row map,
+    compact U_r spread back to the slab layout) holds the same rows in the
+    same order as the fixed-rank stack.  The same store is queried through
+    both (set_xi(0) turns the ragged stack off without touching the stored
+    factors); on the ragged workload's shape (k = 20: both take the same
+    projection kernel) the batch results must be identical, bit for bit."""
+    from paper_1805_00754_gb300 import Store
+    w = synthetic.WORKLOADS["ragged_batch_f32"]
+    A = synthetic.rows(w.series, 0, 9 * w.b + 304).astype(np.float32)
+    T = A.shape[0]
+    ts, te = synthetic.queries(T, 48, 500, 15_000, seed=synthetic.SEED_BASE + 41)
+    st = Store(n=w.series.n, b=w.b, k=w.k, dtype="f32", capacity_rows=T, xi=1.0)
+    st.append(torch.from_numpy(A).cuda())
+    ranks, _, _ = st.block_stats()
+    assert np.all(ranks == w.k)
+    outs = []
+    for xi in (1.0, 0.0):
+        st.set_xi(xi)
+        res = st.query_batch(ts, te)
+        torch.cuda.synchronize()
+        outs.append([(r.U.cpu().numpy(), r.S.cpu().numpy(), r.V.cpu().numpy()) for r in res])
+    assert st.status() == (0, 0) and st.fault() == 0
+    st.close()
+    for q, (a, z) in enumerate(zip(*outs)):
+        for x, y in zip(a, z):
+            np.testing.assert_array_equal(x, y, err_msg=f"query {q}")
+
+
+def _varied_rank_rows(nblk, b, n, dims, seed):
+    """Blocks whose rows span dims[i % len(dims)] directions (Gaussian
+    coefficients on a seeded basis, decaying weights) plus N(0, 1e-4) noise:
+    the energy rule gives them very different ranks."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(nblk):
+        d = dims[i % len(dims)]
+        Q, _ = np.linalg.qr(g.standard_normal((n, d)))
+        wts = 1.0 / np.arange(1, d + 1)
+        out.append((g.standard_normal((b, d)) * wts) @ Q.T + 1e-4 * g.standard_normal((b, n)))
+    return np.vstack(out)
+
+
+def test_ragged_stack_varied_ranks_against_oracle():
+    """Blocks of 2 to 14 signal directions (n = 128, b = 512, k = 16,
+    xi = 0.999): each interior slab stacks only its k_i rows.  Queries over
+    many blocks meet the oracle's queries of its xi store, and in the factored
+    form every coefficient row past a block's k_i is zero (the stack dropped
+    it)."""
+    b, n, k, xi = 512, 128, 16, 0.999
+    A = _varied_rank_rows(24, b, n, (2, 5, 9, 14, 3, 12), synthetic.SEED_BASE + 43)
+    st, exact = _xi_store(A, b, k, "f32", xi)
+    ost = oracle.compress(exact, b, k, xi=xi)
+    ranks = _check_blocks(st, ost, 1e-4)
+    assert min(ranks) <= 3 and max(ranks) >= 12
+    T = A.shape[0]
+    ranges = [(0, T - 1), (100, 9_000), (b - 1, 5 * b), (3 * b + 17, 20 * b - 5), (7 * b, 7 * b + 300)]
+    for a, z in ranges:
+        out = st.query(a, z)
+        torch.cuda.synchronize()
+        compare_query(out, oracle.query(ost, a, z), **F32, label=f"ragged xi [{a},{z}]", ost=ost, ts=a, te=z)
+    fac = st.query_batch_factored(np.array([r[0] for r in ranges]), np.array([r[1] for r in ranges]))
+    torch.cuda.synchronize()
+    for q, (a, z) in enumerate(ranges):
+        S, E = a // b, z // b
+        o = int(fac.offsets[q])
+        C = fac.coef[o:o + (E - S + 1) * k].cpu().numpy()      # k rows per covered block
+        for t in range(1, E - S):                  # interior slabs
+            assert np.all(C[t * k + ranks[S + t]:(t + 1) * k] == 0), (q, t)
+    assert st.status() == (0, 0) and st.fault() == 0
