@@ -196,8 +196,67 @@ __device__ void ra_flush(T* U, int k, int r_old, const T* C, const T* P, int r_p
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_row_append(RowAppendArgs a) {
+// One-sided Jacobi on the rows of M (m <= MR <= 32) by one warp in
+// registers: lane i holds row i of M and column i of J; in each round a lane
+// fetches its partner's row and column by shuffles, both lanes of a pair form
+// the same dot products (same values, same order) and so the same rotation,
+// and each updates its own row and column.  No barrier: rounds are ordered
+// by the warp itself.  prt[r * 32 + i] is lane i's partner in round r (i
+// itself, or an index >= m, when it has none).
+template <typename T, int MR>
+__device__ void ra_jacobi_warp(T* M, T* J, int m, int mm, const int* prt, T tol2, int lane) {
+    T x[MR], jc[MR];
+#pragma unroll
+    for (int c = 0; c < MR; ++c) {
+        x[c] = (lane < m && c < m) ? M[lane * m + c] : T(0);
+        jc[c] = (lane < m && c < m) ? J[c * m + lane] : T(0);
+    }
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        bool any = false;
+        for (int r = 0; r < mm - 1; ++r) {
+            const int j = prt[r * 32 + lane];
+            const int js = j < 32 ? j : lane;                 // shuffle source (no partner: itself)
+            T y[MR];
+            T app = 0, aqq = 0, apq = 0;
+#pragma unroll
+            for (int c = 0; c < MR; ++c) {
+                y[c] = __shfl_sync(0xffffffffu, x[c], js);
+                app += x[c] * x[c];
+                aqq += y[c] * y[c];
+                apq += x[c] * y[c];
+            }
+            const bool isp = lane < j;
+            const T a_pp = isp ? app : aqq, a_qq = isp ? aqq : app;
+            T s = 0, tau = 0;
+            if (lane < m && j < m && j != lane && apq != T(0) && apq * apq > tol2 * (a_pp * a_qq)) {
+                rotation(a_pp, a_qq, apq, s, tau);
+                any = true;
+            }
+            // Rutishauser's form: p' = p - s (q + tau p), q' = q + s (p - tau q),
+            // i.e. own' = own + sg (other + rho own)
+            const T sg = isp ? -s : s, rho = isp ? tau : -tau;
+#pragma unroll
+            for (int c = 0; c < MR; ++c) {
+                const T yj = __shfl_sync(0xffffffffu, jc[c], js);
+                x[c] += sg * (y[c] + rho * x[c]);
+                jc[c] += sg * (yj + rho * jc[c]);
+            }
+        }
+        if (!__any_sync(0xffffffffu, any)) break;
+    }
+    if (lane < m) {
+#pragma unroll
+        for (int c = 0; c < MR; ++c) {
+            if (c < m) {
+                M[lane * m + c] = x[c];
+                J[c * m + lane] = jc[c];
+            }
+        }
+    }
+}
+
+template <typename T, int MR>
+__global__ void __launch_bounds__(MR > 0 ? 256 : 1024) k_row_append(RowAppendArgs a) {
     extern __shared__ __align__(16) unsigned char ras[];
     const int j = blockIdx.x;
     if (j >= a.nblk) return;
@@ -239,10 +298,23 @@ __global__ void __launch_bounds__(1024) k_row_append(RowAppendArgs a) {
     const T tol = T(2) * zsqrt(T(m)) * ra_eps<T>();
     const T tol2 = tol * tol;
     const int g = ra_group(k), jt = ra_jacobi_threads(k);
-    for (int e = tid; e < (mm - 1) * npair; e += nt) {
-        int p, q;
-        rr_pair(mm, e / npair, e % npair, p, q);
-        pairs[e] = p | (q << 16);
+    if constexpr (MR > 0) {
+        // each lane's partner per round (itself where it has none)
+        for (int e = tid; e < (mm - 1) * 32; e += nt) pairs[e] = e & 31;
+        __syncthreads();
+        for (int e = tid; e < (mm - 1) * npair; e += nt) {
+            int p, q;
+            const int r = e / npair;
+            rr_pair(mm, r, e % npair, p, q);
+            pairs[r * 32 + p] = q;
+            if (q < 32) pairs[r * 32 + q] = p;
+        }
+    } else {
+        for (int e = tid; e < (mm - 1) * npair; e += nt) {
+            int p, q;
+            rr_pair(mm, e / npair, e % npair, p, q);
+            pairs[e] = p | (q << 16);
+        }
     }
     // the state: K = diag(sigma) V^T of the rows so far (empty for a new block)
     for (int e = tid; e < k * n; e += nt) K[e] = r0 > 0 ? sig[e / n] * Vt[e] : T(0);
@@ -289,9 +361,12 @@ __global__ void __launch_bounds__(1024) k_row_append(RowAppendArgs a) {
             J[e] = row == col ? T(1) : T(0);
         }
         __syncthreads();
-        // g lanes per pair, all pairs of a round at once; only the first jt
-        // threads (whole warps) take part and synchronise on barrier 1
-        if (tid < jt) {
+        if constexpr (MR > 0) {
+            // m <= 32: one warp in registers (the other warps wait at the barrier)
+            if (warp == 0) ra_jacobi_warp<T, MR>(M, J, m, mm, pairs, tol2, lane);
+        } else if (tid < jt) {
+            // g lanes per pair, all pairs of a round at once; only the first jt
+            // threads (whole warps) take part and synchronise on barrier 1
             const int pi = tid / g, sl = tid - pi * g;
             for (int sweep = 0; sweep < 40; ++sweep) {
                 int any = 0;
@@ -463,23 +538,39 @@ __global__ void __launch_bounds__(1024) k_row_append(RowAppendArgs a) {
 
 size_t row_append_smem_bytes(int n, int k, bool fp64) { return row_append_smem(n, k, fp64 ? 8 : 4); }
 
+// FP32 with m = k + 1 <= 32: the register Jacobi (MR = m rounded up to 8),
+// 256 threads (measured 54 -> 40 us per row at n = 256, k = 16); larger k, and
+// FP64, whose one-warp chains wait on the SM's narrow FP64 pipe (151 -> 279 us
+// per row at k = 8): the block-wide Jacobi
+template <typename T, int MR>
+static cudaError_t row_append_go(const RowAppendArgs& a, size_t sm, cudaStream_t st) {
+    cudaError_t e;
+    if (sm > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_row_append<T, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+        return e;
+    k_row_append<T, MR><<<a.nblk, MR > 0 ? 256 : row_append_threads(a.k), sm, st>>>(a);
+    return cudaSuccess;
+}
+template <typename T>
+static cudaError_t row_append_dispatch(const RowAppendArgs& a, size_t sm, cudaStream_t st) {
+    const int m = a.k + 1;
+    if constexpr (sizeof(T) == 8) {
+        return row_append_go<T, 0>(a, sm, st);
+    } else {
+        if (m <= 8) return row_append_go<T, 8>(a, sm, st);
+        if (m <= 16) return row_append_go<T, 16>(a, sm, st);
+        if (m <= 24) return row_append_go<T, 24>(a, sm, st);
+        if (m <= 32) return row_append_go<T, 32>(a, sm, st);
+        return row_append_go<T, 0>(a, sm, st);
+    }
+}
+
 cudaError_t launch_row_append(const RowAppendArgs& a, bool fp64, cudaStream_t st) {
     if (a.nblk < 1) return cudaSuccess;
     const size_t sm = row_append_smem(a.n, a.k, fp64 ? 8 : 4);
-    cudaError_t e;
-    if (fp64) {
-        if (sm > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_row_append<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-                cudaSuccess)
-            return e;
-        k_row_append<double><<<a.nblk, row_append_threads(a.k), sm, st>>>(a);
-    } else {
-        if (sm > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(k_row_append<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-                cudaSuccess)
-            return e;
-        k_row_append<float><<<a.nblk, row_append_threads(a.k), sm, st>>>(a);
-    }
+    cudaError_t e = fp64 ? row_append_dispatch<double>(a, sm, st) : row_append_dispatch<float>(a, sm, st);
+    if (e != cudaSuccess) return e;
     note_launches(1);
     return cudaGetLastError();
 }
