@@ -194,9 +194,12 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
     const bool diag = (ti == tj);
     const int64_t ld = src.ld();
     const bool vec = std::is_same<Tin, float>::value && (ld % 4 == 0) && (n % 4 == 0);
+    const bool vecb = std::is_same<Tin, __nv_bfloat16>::value && (ld % 4 == 0) && (n % 4 == 0);
     for (int item = blockIdx.y; item < src.count(); item += gridDim.y) {
         const Tin* X = (const Tin*)src.X(item, sizeof(Tin));
         const bool xal = vec && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+        // bf16 rows: four values as one 8-byte load, kept as they are (exact in bf16)
+        const bool xalb = vecb && ((reinterpret_cast<uintptr_t>(X) & 7) == 0);
         const auto cx = src.ctx(item, sizeof(Tin));
         const int rows = src.rows(item);
         float acc[4][4][4];
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
         // the next 32-row chunk in registers while the current one is multiplied.
         const int npnl = diag ? 1 : 2;
         float pre[2][4][4];
+        uint2 preb[2][4];
         auto fetch = [&](int r0) {
 #pragma unroll
             for (int pnl = 0; pnl < 2; ++pnl) {
@@ -221,6 +225,17 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
                     const int r = f >> 5, c = (f & 31) * 4, gr = r0 + r, gc = P0 + c;
                     float* v = pre[pnl][g];
                     v[0] = v[1] = v[2] = v[3] = 0.f;
+                    if constexpr (std::is_same<Tin, __nv_bfloat16>::value) {
+                        if (xalb) {
+                            uint2 q = make_uint2(0u, 0u);
+                            if (gr < rows && gc < n) {
+                                float sc = 1.f;
+                                q = *reinterpret_cast<const uint2*>(src.template row<Tin>(cx, gr, sc) + gc);
+                            }
+                            preb[pnl][g] = q;
+                            continue;
+                        }
+                    }
                     if (gr < rows) {
                         float sc = 1.f;
                         const Tin* src_p = src.template row<Tin>(cx, gr, sc) + gc;
@@ -255,6 +270,11 @@ __global__ void __launch_bounds__(256, 1) k_gram_lo(Src src, TcScratch sc, int n
                     const int r = f >> 5, c = (f & 31) * 4;
                     const float* v = pre[pnl][g];
                     uint32_t* dp = reinterpret_cast<uint32_t*>(D + r * LDS + c);
+                    if (std::is_same<Tin, __nv_bfloat16>::value && xalb) {
+                        dp[0] = preb[pnl][g].x;
+                        dp[1] = preb[pnl][g].y;
+                        continue;
+                    }
                     dp[0] = pack_bf16(__float2bfloat16_rn(v[0]), __float2bfloat16_rn(v[1]));
                     dp[1] = pack_bf16(__float2bfloat16_rn(v[2]), __float2bfloat16_rn(v[3]));
                 }
