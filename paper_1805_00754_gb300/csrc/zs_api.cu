@@ -110,7 +110,7 @@ zs_status QueryExec::reserve(const zs_store& st, int nq, int64_t nslab, int kq) 
     if ((s = al(&vr, ts * (size_t)want_nq * want_kq * n, "v")) != ZS_OK) return s;
     if ((s = al(&tco, ts * (size_t)2 * want_nq * k * k, "partial")) != ZS_OK) return s;
     if ((s = al(&C, ts * want_sl * k * want_kq, "lift coeff")) != ZS_OK) return s;
-    ews_ctas = std::max(1, st.num_sms);
+    ews_ctas = std::max(1, st.num_sms) * (st.fp64 ? 1 : 2);   // float: two subspace CTAs per SM
     aux_tiles = (int64_t)want_sl * k / 128 + want_nq;
     if ((s = al(&ews, eig_ws_bytes((int)n, st.fp64, ews_ctas), "eigen workspace")) != ZS_OK) return s;
     if (use_tc_path(st.fp64, (int)n, st.cfg.flags)) {
@@ -377,7 +377,7 @@ static zs_status store_alloc(zs_store* st) {
                     "Rayleigh-Ritz scratch")) != ZS_OK)
             return s;
     }
-    st->ews_ctas = std::max(1, st->num_sms);
+    st->ews_ctas = std::max(1, st->num_sms) * (st->fp64 ? 1 : 2);   // float: two subspace CTAs per SM
     if ((s = al(&st->ews, eig_ws_bytes((int)c.n, st->fp64, st->ews_ctas), "eigen workspace")) != ZS_OK) return s;
     // host staging: two device buffers of whole blocks
     const size_t blk_bytes = st->insize * (size_t)c.b * c.n;

@@ -679,16 +679,49 @@ __global__ void __launch_bounds__(256) k_partial(QueryArgs a) {
         __syncthreads();
         // slab rows of M
         T* Ms = (T*)a.M + (P.slab0 + t) * k * n;
-        for (int e = tid; e < k * n; e += nt) {
-            const int j = e / n, l = e - (e / n) * n;
-            T v = T(0);
-            if (st[j] > T(0)) {
-                TR accv = 0;
-                const int pj = es.perm[j];
-                for (int aa = 0; aa < ki; ++aa) accv += Zo[aa * ld + pj] * (TR)vt[(int64_t)aa * n + l];
-                v = st[j] * (T)accv;
+        if constexpr (REF && std::is_same<T, float>::value) {
+            // The FP64 eigenvectors split into two floats each (z = zh + zl to
+            // ~2^-48 relative), columns in sorted order, in the FP32 tiles that
+            // the eigensolver no longer needs; each dot product then runs at
+            // the FP32 rate with the exact-product / TwoSum sum used for H above
+            float* Zh = se.A_T;
+            float* Zl = se.Z_T;
+            for (int e = tid; e < ki * ki; e += nt) {
+                const int aa = e / ki, j = e - (e / ki) * ki;
+                const double z = Zo[aa * ld + es.perm[j]];
+                const float h = (float)z;
+                Zh[aa * ld + j] = h;
+                Zl[aa * ld + j] = (float)(z - (double)h);
             }
-            Ms[e] = v;
+            __syncthreads();
+            for (int e = tid; e < k * n; e += nt) {
+                const int j = e / n, l = e - (e / n) * n;
+                float v = 0.f;
+                if (st[j] > 0.f) {
+                    float hi = 0.f, lo = 0.f;
+                    for (int aa = 0; aa < ki; ++aa) {
+                        const float x = vt[(int64_t)aa * n + l], zh = Zh[aa * ld + j];
+                        const float pr = zh * x, pe = fmaf(zh, x, -pr);
+                        const float sm = hi + pr, bb = sm - hi;
+                        lo += ((hi - (sm - bb)) + (pr - bb)) + fmaf(Zl[aa * ld + j], x, pe);
+                        hi = sm;
+                    }
+                    v = st[j] * (hi + lo);
+                }
+                Ms[e] = v;
+            }
+        } else {
+            for (int e = tid; e < k * n; e += nt) {
+                const int j = e / n, l = e - (e / n) * n;
+                T v = T(0);
+                if (st[j] > T(0)) {
+                    TR accv = 0;
+                    const int pj = es.perm[j];
+                    for (int aa = 0; aa < ki; ++aa) accv += Zo[aa * ld + pj] * (TR)vt[(int64_t)aa * n + l];
+                    v = st[j] * (T)accv;
+                }
+                Ms[e] = v;
+            }
         }
         // lift coefficients Sigma V~ Sigma~^{-1}  (k x k)
         T* tc = (T*)a.tco + (int64_t)p * k * k;

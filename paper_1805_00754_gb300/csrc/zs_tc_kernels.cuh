@@ -359,26 +359,43 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
         __syncthreads();
         mgs_orth<float>(Q, ldq, n, m, red, coef);
         for (int it = 0; it < sc.power_its; ++it) {
-            for (int i = tid; i < n; i += nt) {
-                float acc[MB];
+            // Y = G~ Q~ in register tiles of 4 rows x 8 columns per thread.
+            // G~ is symmetric, so row l of G~ holds the l-th coefficient of
+            // rows i0..i0+3: one 16-byte load feeds 32 fused multiply-adds.
+            const int cgn = (m + 7) >> 3, tasks = ((n + 3) >> 2) * cgn;
+            const bool vec = (n & 3) == 0;
+            for (int t = tid; t < tasks; t += nt) {
+                const int rg = t / cgn, c0 = (t - rg * cgn) * 8, i0 = rg * 4;
+                float acc[4][8];
 #pragma unroll
-                for (int c = 0; c < MB; ++c) acc[c] = 0.f;
-                for (int l0 = 0; l0 < n; l0 += 8) {
-                    float g[8];
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) g[u] = (l0 + u < n) ? __ldg(G + (size_t)(l0 + u) * n + i) : 0.f;
+                    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+                const float* Gc = G + i0;
+#pragma unroll 2
+                for (int l = 0; l < n; ++l) {
+                    float g[4];
+                    if (vec) {
+                        const float4 v = __ldg(reinterpret_cast<const float4*>(Gc + (size_t)l * n));
+                        g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
+                    } else {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (l0 + u >= n) break;
-                        const float* qr = Q + (l0 + u) * ldq;
-#pragma unroll
-                        for (int c = 0; c < MB; ++c)
-                            if (c < m) acc[c] += g[u] * qr[c];
+                        for (int r = 0; r < 4; ++r) g[r] = (i0 + r < n) ? __ldg(Gc + (size_t)l * n + r) : 0.f;
                     }
+                    const float* qr = Q + l * ldq + c0;
+                    float q[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) q[c] = (c0 + c < m) ? qr[c] : 0.f;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(g[r], q[c], acc[r][c]);
                 }
 #pragma unroll
-                for (int c = 0; c < MB; ++c)
-                    if (c < m) Y[i * ldq + c] = acc[c];
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (i0 + r < n && c0 + c < m) Y[(i0 + r) * ldq + c0 + c] = acc[r][c];
             }
             __syncthreads();
             for (int e = tid; e < n * m; e += nt) {
