@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #ifndef ZS_MAXM
 #define ZS_MAXM 64
 #endif
@@ -99,6 +101,14 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
     const int tid = threadIdx.x, nt = blockDim.x;
     if (init_z)
         for (int e = tid; e < m * m; e += nt) Z[(e / m) * ldz + (e % m)] = (e / m == e % m) ? T(1) : T(0);
+    // FP32: the upper triangle defines A, and the 2 x 2 block updates below
+    // keep both halves equal
+    constexpr bool kBlock = std::is_same<T, float>::value;
+    if (kBlock)
+        for (int e = tid; e < m * m; e += nt) {
+            const int p = e / m, q = e - (e / m) * m;
+            if (q < p) A[p * lda + q] = A[q * lda + p];
+        }
     if (tid == 0) {
         T mx = 0;
         for (int i = 0; i < m; ++i) mx = fmax(mx, zabs(A[i * lda + i]));
@@ -119,8 +129,18 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
     const T floor_ = (sizeof(T) == 4 ? floor_mult : T(1)) * eps_of<T>() * js.scale;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
+        // a sweep starts only if some pair is still above the thresholds (a
+        // sweep without rotations would leave A as it is)
         if (tid == 0) js.flag = 0;
         __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            const int p = e / m, q = e - (e / m) * m;
+            if (q <= p) continue;
+            const T aa = zabs(A[p * lda + q]);
+            if (aa > floor_ && aa > tol * zsqrt(zabs(A[p * lda + p] * A[q * lda + q]))) js.flag = 1;
+        }
+        __syncthreads();
+        if (!js.flag) break;
         for (int r = 0; r < mm - 1; ++r) {
             for (int i = tid; i < np; i += nt) {
                 int p, q;
@@ -134,7 +154,6 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
                         const T t = (tau >= T(0) ? T(1) : T(-1)) / (zabs(tau) + zsqrt(T(1) + tau * tau));
                         c = T(1) / zsqrt(T(1) + t * t);
                         s = t * c;
-                        js.flag = 1;
                     }
                 }
                 js.pq[2 * i] = p;
@@ -143,37 +162,79 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
                 js.cs[2 * i + 1] = s;
             }
             __syncthreads();
-            // rows:  A <- J^T A
-            for (int e = tid; e < np * m; e += nt) {
-                const int i = e / m, j = e - (e / m) * m;
-                const T s = js.cs[2 * i + 1];
-                if (s == T(0)) continue;
-                const T c = js.cs[2 * i];
-                const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
-                const T ap = A[p * lda + j], aq = A[q * lda + j];
-                A[p * lda + j] = c * ap - s * aq;
-                A[q * lda + j] = s * ap + c * aq;
+            if (!kBlock) {
+                // FP64: rows A <- J^T A, then columns A <- A J and Z <- Z J
+                for (int e = tid; e < np * m; e += nt) {
+                    const int i = e / m, j = e - (e / m) * m;
+                    const T s = js.cs[2 * i + 1];
+                    if (s == T(0)) continue;
+                    const T c = js.cs[2 * i];
+                    const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
+                    const T ap = A[p * lda + j], aq = A[q * lda + j];
+                    A[p * lda + j] = c * ap - s * aq;
+                    A[q * lda + j] = s * ap + c * aq;
+                }
+                __syncthreads();
+                for (int e = tid; e < np * m; e += nt) {
+                    const int i = e / m, row = e - (e / m) * m;
+                    const T s = js.cs[2 * i + 1];
+                    if (s == T(0)) continue;
+                    const T c = js.cs[2 * i];
+                    const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
+                    const T ap = A[row * lda + p], aq = A[row * lda + q];
+                    A[row * lda + p] = c * ap - s * aq;
+                    A[row * lda + q] = s * ap + c * aq;
+                    const T zp = Z[row * ldz + p], zq = Z[row * ldz + q];
+                    Z[row * ldz + p] = c * zp - s * zq;
+                    Z[row * ldz + q] = s * zp + c * zq;
+                }
+                __syncthreads();
+                continue;
             }
-            __syncthreads();
-            // columns: A <- A J,  Z <- Z J
+            // FP32: A <- J^T A J one 2 x 2 block at a time: block (i, j) of the pairs
+            // (rows p_i, q_i; columns p_j, q_j) becomes R_i B R_j^T, written
+            // with its mirror (j, i), so A stays exactly symmetric.  The blocks
+            // partition A, so the updates are independent and run in place.
+            for (int e = tid; e < np * np; e += nt) {
+                const int i = e / np, j = e - (e / np) * np;
+                if (i > j) continue;
+                const T si = js.cs[2 * i + 1], sj = js.cs[2 * j + 1];
+                if (si == T(0) && sj == T(0)) continue;
+                const T ci = js.cs[2 * i], cj = js.cs[2 * j];
+                const int p = js.pq[2 * i], q = js.pq[2 * i + 1], u = js.pq[2 * j], v = js.pq[2 * j + 1];
+                const bool hq = q < m, hv = v < m;
+                const T a00 = A[p * lda + u];
+                const T a01 = hv ? A[p * lda + v] : T(0);
+                const T a10 = hq ? A[q * lda + u] : T(0);
+                const T a11 = (hq && hv) ? A[q * lda + v] : T(0);
+                const T b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
+                const T b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
+                const T d00 = cj * b00 - sj * b01, d01 = sj * b00 + cj * b01;
+                const T d10 = cj * b10 - sj * b11, d11 = sj * b10 + cj * b11;
+                A[p * lda + u] = d00;
+                if (hv) A[p * lda + v] = d01;
+                if (hq) A[q * lda + u] = d10;
+                if (hq && hv) A[q * lda + v] = d11;
+                if (i != j) {
+                    A[u * lda + p] = d00;
+                    if (hv) A[v * lda + p] = d01;
+                    if (hq) A[u * lda + q] = d10;
+                    if (hq && hv) A[v * lda + q] = d11;
+                }
+            }
+            // Z <- Z J
             for (int e = tid; e < np * m; e += nt) {
                 const int i = e / m, row = e - (e / m) * m;
                 const T s = js.cs[2 * i + 1];
                 if (s == T(0)) continue;
                 const T c = js.cs[2 * i];
                 const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
-                const T ap = A[row * lda + p], aq = A[row * lda + q];
-                A[row * lda + p] = c * ap - s * aq;
-                A[row * lda + q] = s * ap + c * aq;
                 const T zp = Z[row * ldz + p], zq = Z[row * ldz + q];
                 Z[row * ldz + p] = c * zp - s * zq;
                 Z[row * ldz + q] = s * zp + c * zq;
             }
             __syncthreads();
         }
-        const int f = js.flag;
-        __syncthreads();
-        if (!f) break;
     }
     return sweep;
 }

@@ -352,9 +352,21 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
             if (rk < m) piv[rk] = i;
         }
         __syncthreads();
-        for (int e = tid; e < n * m; e += nt) {
-            const int c = e / n, i = e - (e / n) * n;
-            Q[i * ldq + c] = G[(size_t)piv[c] * n + i];
+        // the pivoted columns of G~, eight loads in flight per thread
+        for (int e0 = tid; e0 < n * m; e0 += 8 * nt) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * nt;
+                const int c = e / n, i = e - (e / n) * n;
+                v[u] = e < n * m ? __ldg(G + (size_t)piv[c] * n + i) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = e0 + u * nt;
+                const int c = e / n, i = e - (e / n) * n;
+                if (e < n * m) Q[i * ldq + c] = v[u];
+            }
         }
         __syncthreads();
         mgs_orth<float>(Q, ldq, n, m, red, coef);
@@ -372,24 +384,36 @@ __global__ void __launch_bounds__(256) k_subspace(Src src, TcScratch sc, int n, 
 #pragma unroll
                     for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
                 const float* Gc = G + i0;
-#pragma unroll 2
-                for (int l = 0; l < n; ++l) {
-                    float g[4];
-                    if (vec) {
-                        const float4 v = __ldg(reinterpret_cast<const float4*>(Gc + (size_t)l * n));
-                        g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
-                    } else {
+                // eight rows of G~ in flight per thread: the loop is bound by
+                // the latency of these loads, not by the multiply-adds
+                for (int l0 = 0; l0 < n; l0 += 8) {
+                    const int lim = min(8, n - l0);
+                    float g[8][4];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) g[r] = (i0 + r < n) ? __ldg(Gc + (size_t)l * n + r) : 0.f;
+                    for (int u = 0; u < 8; ++u) {
+                        const float* gr = Gc + (size_t)(l0 + u) * n;
+                        if (vec) {
+                            const float4 v = u < lim ? __ldg(reinterpret_cast<const float4*>(gr))
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                            g[u][0] = v.x; g[u][1] = v.y; g[u][2] = v.z; g[u][3] = v.w;
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) g[u][r] = (u < lim && i0 + r < n) ? __ldg(gr + r) : 0.f;
+                        }
                     }
-                    const float* qr = Q + l * ldq + c0;
-                    float q[8];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) q[c] = (c0 + c < m) ? qr[c] : 0.f;
+                    for (int u = 0; u < 8; ++u) {
+                        if (u < lim) {
+                            const float* qr = Q + (l0 + u) * ldq + c0;
+                            float q[8];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                            for (int c = 0; c < 8; ++c) q[c] = (c0 + c < m) ? qr[c] : 0.f;
 #pragma unroll
-                        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(g[r], q[c], acc[r][c]);
+                            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                                for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(g[u][r], q[c], acc[r][c]);
+                        }
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
@@ -1420,7 +1444,15 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
         const float* Cq = sc.Cq + (size_t)item * m * m;
         for (int e = tid; e < m * m; e += nt) {
             TR h = 0;
-            for (int t = 0; t < ntiles; ++t) h += (TR)Hp[(size_t)t * m * m + e];
+            // tile partials in fixed order, eight loads in flight
+            for (int t0 = 0; t0 < ntiles; t0 += 8) {
+                float hv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) hv[u] = t0 + u < ntiles ? __ldg(Hp + (size_t)(t0 + u) * m * m + e) : 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (t0 + u < ntiles) h += (TR)hv[u];
+            }
             Hs[(e / m) * ld + e % m] = h;
             Cs[(e / m) * ld + e % m] = (TR)Cq[e];
         }
