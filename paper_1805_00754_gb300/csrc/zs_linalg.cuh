@@ -95,6 +95,7 @@ struct JacobiScratch {
 // diagonal of A holds the eigenvalues (unsorted) and the columns of Z the
 // eigenvectors.  If init_z, Z starts as the identity, else the rotations are
 // accumulated into the Z given (warm start / refinement).  Returns sweeps used.
+// The CTA needs at least m/2 + 1 threads (all callers run 128 or more, m <= 64).
 template <typename T>
 __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>& js,
                           int max_sweeps, bool init_z, T floor_mult = T(64)) {
@@ -195,43 +196,58 @@ __device__ int jacobi_eig(T* A, int lda, T* Z, int ldz, int m, JacobiScratch<T>&
             // (rows p_i, q_i; columns p_j, q_j) becomes R_i B R_j^T, written
             // with its mirror (j, i), so A stays exactly symmetric.  The blocks
             // partition A, so the updates are independent and run in place.
-            for (int e = tid; e < np * np; e += nt) {
-                const int i = e / np, j = e - (e / np) * np;
-                if (i > j) continue;
-                const T si = js.cs[2 * i + 1], sj = js.cs[2 * j + 1];
-                if (si == T(0) && sj == T(0)) continue;
-                const T ci = js.cs[2 * i], cj = js.cs[2 * j];
-                const int p = js.pq[2 * i], q = js.pq[2 * i + 1], u = js.pq[2 * j], v = js.pq[2 * j + 1];
-                const bool hq = q < m, hv = v < m;
-                const T a00 = A[p * lda + u];
-                const T a01 = hv ? A[p * lda + v] : T(0);
-                const T a10 = hq ? A[q * lda + u] : T(0);
-                const T a11 = (hq && hv) ? A[q * lda + v] : T(0);
-                const T b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
-                const T b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
-                const T d00 = cj * b00 - sj * b01, d01 = sj * b00 + cj * b01;
-                const T d10 = cj * b10 - sj * b11, d11 = sj * b10 + cj * b11;
-                A[p * lda + u] = d00;
-                if (hv) A[p * lda + v] = d01;
-                if (hq) A[q * lda + u] = d10;
-                if (hq && hv) A[q * lda + v] = d11;
-                if (i != j) {
-                    A[u * lda + p] = d00;
-                    if (hv) A[v * lda + p] = d01;
-                    if (hq) A[u * lda + q] = d10;
-                    if (hq && hv) A[v * lda + q] = d11;
+            // Thread t takes column pair j = t mod np and row pairs i = t / np,
+            // t / np + ng, ... (i <= j); then rows of Z for pair j likewise.
+            const int ng = nt / np;
+            if (tid < ng * np) {
+                const int j = tid % np, g = tid / np;
+                const T sj = js.cs[2 * j + 1], cj = js.cs[2 * j];
+                const int u = js.pq[2 * j], v = js.pq[2 * j + 1];
+                const bool hv = v < m;
+                for (int i = g; i <= j; i += ng) {
+                    const T si = js.cs[2 * i + 1];
+                    if (si == T(0) && sj == T(0)) continue;
+                    const T ci = js.cs[2 * i];
+                    const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
+                    const bool hq = q < m;
+                    const T a00 = A[p * lda + u];
+                    const T a01 = hv ? A[p * lda + v] : T(0);
+                    const T a10 = hq ? A[q * lda + u] : T(0);
+                    const T a11 = (hq && hv) ? A[q * lda + v] : T(0);
+                    const T b00 = ci * a00 - si * a10, b01 = ci * a01 - si * a11;
+                    const T b10 = si * a00 + ci * a10, b11 = si * a01 + ci * a11;
+                    const T d00 = cj * b00 - sj * b01, d01 = sj * b00 + cj * b01;
+                    const T d10 = cj * b10 - sj * b11, d11 = sj * b10 + cj * b11;
+                    A[p * lda + u] = d00;
+                    if (hv) A[p * lda + v] = d01;
+                    if (hq) A[q * lda + u] = d10;
+                    if (hq && hv) A[q * lda + v] = d11;
+                    if (i != j) {
+                        A[u * lda + p] = d00;
+                        if (hv) A[v * lda + p] = d01;
+                        if (hq) A[u * lda + q] = d10;
+                        if (hq && hv) A[v * lda + q] = d11;
+                    }
                 }
-            }
-            // Z <- Z J
-            for (int e = tid; e < np * m; e += nt) {
-                const int i = e / m, row = e - (e / m) * m;
-                const T s = js.cs[2 * i + 1];
-                if (s == T(0)) continue;
-                const T c = js.cs[2 * i];
-                const int p = js.pq[2 * i], q = js.pq[2 * i + 1];
-                const T zp = Z[row * ldz + p], zq = Z[row * ldz + q];
-                Z[row * ldz + p] = c * zp - s * zq;
-                Z[row * ldz + q] = s * zp + c * zq;
+                // Z <- Z J for pair j, four rows' loads issued together
+                if (sj != T(0))
+                    for (int r0 = g; r0 < m; r0 += 4 * ng) {
+                        T zp[4], zq[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int row = r0 + h * ng;
+                            zp[h] = row < m ? Z[row * ldz + u] : T(0);
+                            zq[h] = row < m ? Z[row * ldz + v] : T(0);
+                        }
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int row = r0 + h * ng;
+                            if (row < m) {
+                                Z[row * ldz + u] = cj * zp[h] - sj * zq[h];
+                                Z[row * ldz + v] = sj * zp[h] + cj * zq[h];
+                            }
+                        }
+                    }
             }
             __syncthreads();
         }

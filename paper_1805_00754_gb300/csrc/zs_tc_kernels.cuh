@@ -1413,9 +1413,9 @@ template <bool REF>
 __host__ __device__ __forceinline__ size_t rr_warp_bytes(int m) {
     const size_t ld = m + 1;
     const size_t tr = REF ? 8 : 4;
-    // Hs, Cs(L), Li in TR; A_T, Z_T in float; REF: X, W in double
-    size_t b = 3 * tr * m * ld + 2 * 4 * m * ld + (REF ? 2 * 8 * m * ld : 0) + 4 * 64 + 8 * 64 +
-               sizeof(WarpRot<float>) + sizeof(WarpRot<double>) + 32;
+    // Hs, Cs(L), Li in TR; A_T, Z_T in float (+ 4 bytes to align X); REF: X in
+    // double (W shares Cs, which is free once H' is formed); perm, theta
+    size_t b = 3 * tr * m * ld + 2 * 4 * m * ld + 8 + (REF ? 8 * m * ld : 0) + 4 * 64 + 8 * 64;
     return (b + 15) & ~size_t(15);
 }
 
@@ -1433,7 +1433,7 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
     float* A_T = (float*)(Li + (size_t)m * ld);
     float* Z_T = A_T + (size_t)m * ld;
     double* X = (double*)(Z_T + (size_t)m * ld + ((m * ld) & 1));
-    double* W = X + (REF ? (size_t)m * ld : 0);
+    double* W = REF ? (double*)Cs : nullptr;       // refinement rotations, after H' is formed
     int* perm = (int*)(base + rr_warp_bytes<REF>(m) - 4 * 64 - 8 * 64);
     double* thd = (double*)(base + rr_warp_bytes<REF>(m) - 8 * 64);
     const int count = src.count();
@@ -1457,29 +1457,42 @@ __global__ void __launch_bounds__(128) k_rr_core(Src src, TcScratch sc, int kw) 
             Cs[(e / m) * ld + e % m] = (TR)Cq[e];
         }
         __syncthreads();
-        // Cholesky C = L L^T (lower, in place)
+        // Cholesky C = L L^T (lower, in place), right-looking: step j takes the
+        // pivot's square root, scales column j, then updates the trailing
+        // triangle in parallel.  Each entry receives its updates in the order
+        // p = 0, 1, ..., as in the dot-product form.
         for (int j = 0; j < m; ++j) {
             if (tid == 0) {
-                TR d = Cs[j * ld + j];
-                for (int p = 0; p < j; ++p) d -= Cs[j * ld + p] * Cs[j * ld + p];
+                const TR d = Cs[j * ld + j];
                 Cs[j * ld + j] = d > TR(1e-12) ? (TR)sqrt((double)d) : TR(1e-6);
             }
             __syncthreads();
-            for (int i = j + 1 + tid; i < m; i += nt) {
-                TR d = Cs[i * ld + j];
-                for (int p = 0; p < j; ++p) d -= Cs[i * ld + p] * Cs[j * ld + p];
-                Cs[i * ld + j] = d / Cs[j * ld + j];
+            for (int i = j + 1 + tid; i < m; i += nt) Cs[i * ld + j] = Cs[i * ld + j] / Cs[j * ld + j];
+            __syncthreads();
+            const int w = m - 1 - j;                      // trailing order
+            for (int e = tid; e < w * w; e += nt) {
+                const int i = j + 1 + e / w, k = j + 1 + (e - (e / w) * w);
+                if (k <= i) Cs[i * ld + k] -= Cs[i * ld + j] * Cs[k * ld + j];
             }
             __syncthreads();
         }
-        for (int c = tid; c < m; c += nt)
-            for (int i = 0; i < m; ++i) {
-                if (i < c) { Li[i * ld + c] = 0; continue; }
-                TR d = (i == c) ? TR(1) : TR(0);
-                for (int p = c; p < i; ++p) d -= Cs[i * ld + p] * Li[p * ld + c];
-                Li[i * ld + c] = d / Cs[i * ld + i];
-            }
+        // L^-1 by right-looking forward substitution on all columns at once:
+        // step p divides row p, then removes it from the rows below
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, c = e - (e / m) * m;
+            Li[i * ld + c] = (i == c) ? TR(1) : TR(0);
+        }
         __syncthreads();
+        for (int p = 0; p < m; ++p) {
+            for (int c = tid; c <= p; c += nt) Li[p * ld + c] = Li[p * ld + c] / Cs[p * ld + p];
+            __syncthreads();
+            const int rws = m - 1 - p, cls = p + 1;
+            for (int e = tid; e < rws * cls; e += nt) {
+                const int i = p + 1 + e / cls, c = e - (e / cls) * cls;
+                Li[i * ld + c] -= Cs[i * ld + p] * Li[p * ld + c];
+            }
+            __syncthreads();
+        }
         // H' = L^-1 H L^-T  (temp in Cs, L no longer needed)
         for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, c = e % m;
